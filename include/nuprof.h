@@ -1,0 +1,240 @@
+/*
+ * nuprof.h -- C-ABI of the GB300 (sm_103a) relic-overdensity library.
+ *
+ * The library computes the present-day number-density profile n/nbar of a
+ * non-cold relic (massive neutrinos by default) around a spherically symmetric,
+ * growing, mass-compensated NFW dark-matter halo in a flat FRW background, by
+ * the backward N-1-body method of Worku, Sabti & Kamionkowski (arXiv:2410.08267):
+ *
+ *   1. halo derivation: R, z_i, r200, r_s, I(c) from (M_h, c)        Sec. II.B
+ *   2. one test-particle trajectory per (radius x0, momentum |P0|, direction
+ *      mu = cos psi), started at x = (x0, 0), v = v0 (mu, sin psi)   Sec. II.C
+ *   3. integration of the equations of motion backward from z0 = 0 to
+ *      z_end through the closed-form potential gradient            Eq. eoms, App. A
+ *      (classical RK4 in u = ln a with a fixed number of steps)
+ *   4. Liouville map f0(x0, P0, mu) = f_init(P_i)                 Sec. II.C
+ *   5. momentum/direction quadrature divided by the background    Eq. localdensity
+ *
+ * All work runs in hand-written CUDA kernels on one GPU.  There is no CPU
+ * fallback: every entry point that needs the device returns NU_ECUDA when no
+ * usable GPU is present.
+ *
+ * Conventions used by every entry point:
+ *   - Units: comoving length in kpc, velocity in km/s, mass in Msun, relic
+ *     mass in eV, momentum q in units of k_B T0.  Physical constants are fixed
+ *     inside the library: G = 4.30091727e-6 kpc (km/s)^2/Msun,
+ *     c = 299792.458 km/s, k_B = 8.617333262e-5 eV/K, H0 = 0.1 h km/s/kpc.
+ *   - Gravity is attractive: the printed signs of the Poisson equation and of
+ *     App. A are read as a typo (together with Eq. eoms they would repel).
+ *   - Return values: NU_OK (0) on success, a negative NU_E* code otherwise;
+ *     nu_strerror() names it.  On failure no output argument is written.
+ *   - Ownership: every pointer argument is borrowed for the duration of the
+ *     call only; the library copies what it keeps.  Handles returned through
+ *     `out` arguments are owned by the caller and released by the matching
+ *     *_destroy call.
+ *   - Streams are passed as `void*` holding a cudaStream_t (NULL = the legacy
+ *     default stream).  Calls on one handle must not overlap in time on
+ *     different streams (they share the handle's device buffers).
+ *   - Threading: distinct handles may be used from distinct host threads.
+ */
+#ifndef NUPROF_H
+#define NUPROF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Every entry point is exported from the shared library with default visibility. */
+#if defined(__GNUC__)
+#define NU_API __attribute__((visibility("default")))
+#else
+#define NU_API
+#endif
+
+#define NU_VERSION_MAJOR 1
+#define NU_VERSION_MINOR 0
+#define NU_VERSION_PATCH 0
+
+/* ---- error codes ---------------------------------------------------------- */
+#define NU_OK          0
+#define NU_EINVAL     -1   /* an argument is out of range or inconsistent      */
+#define NU_ENOMEM     -2   /* device or host allocation failed / over budget   */
+#define NU_ECUDA      -3   /* a CUDA runtime call failed (no GPU, launch error) */
+#define NU_EBUSY      -4   /* result asked for before any run was enqueued     */
+#define NU_ETIMEDOUT  -5   /* a bounded wait ran out                           */
+#define NU_EDEVICE    -6   /* the device status word reports a non-finite sum  */
+#define NU_ENOTSUP    -7   /* valid but unsupported combination                */
+#define NU_ECANCELED  -8   /* serving: the request was cancelled               */
+#define NU_EAGAIN     -9   /* serving: the request is not finished yet         */
+
+/* ---- halo growth xi(z) (Eq. rhototal; Sec. IV.A variants) ------------------ */
+#define NU_XI_STATIC  0    /* xi = 1 at every z: the NFW halo exists throughout */
+#define NU_XI_LINEAR  1    /* xi = clamp((z_s - z)/(z_s - z_e), 0, 1)^alpha;
+                              xi_p = {alpha (<=0 -> 1), z_s (<=0 -> z_i), z_e (<=0 -> z0)} */
+#define NU_XI_EXP     2    /* xi = exp(-lambda z); xi_p[0] = lambda (mass history M0 e^{-lambda z}) */
+
+/* ---- coupling kappa(z) multiplying G (Sec. IV.B) --------------------------- */
+#define NU_KAPPA_ONE    0  /* kappa = 1                                       */
+#define NU_KAPPA_POW1PZ 1  /* kappa = (1+z)^gamma = a^-gamma; kappa_p[0] = gamma */
+#define NU_KAPPA_PAPER  2  /* kappa = 1 + alpha (z/(1+z))^beta; kappa_p = {alpha, beta} */
+#define NU_KAPPA_CONST  3  /* kappa = kappa_p[0]                              */
+
+/* ---- initial relic distribution f(q), q = P / (k_B T0) (Sec. II.C, IV.B) -- */
+#define NU_F_FD        0   /* Fermi-Dirac 1/(1+exp(q - eta)); f_p[0] = eta     */
+#define NU_F_FREEZEIN  1   /* non-thermal q^(-1/2) exp(-q)                     */
+
+/* ---- precision modes ------------------------------------------------------ */
+#define NU_FP64   0        /* state, force, f and sums in FP64                 */
+#define NU_MIXED  1        /* FP32 state and force; time from an FP64-built
+                              table; f in FP32; quadrature sums in FP64        */
+
+/* ---- radius units ---------------------------------------------------------- */
+#define NU_RADII_KPC   0   /* comoving kpc                                     */
+#define NU_RADII_R200  1   /* units of r200, the physical virial radius at z0  */
+
+/* ---- option flags ---------------------------------------------------------- */
+#define NU_FLAG_KEEP_QI  1 /* keep the final momentum q_i of every trajectory
+                              (phase-space integrand, Fig. 3 of the paper)     */
+#define NU_FLAG_GRAPH    2 /* batches: capture the launch in a CUDA graph      */
+
+typedef struct nu_cosmo {
+    double Om;       /* matter density today; Omega_Lambda = 1 - Om (Sec. II.A) */
+    double h;        /* H0 = 100 h km/s/Mpc                                    */
+    double T0_K;     /* relic temperature today, 1.95 K for neutrinos          */
+} nu_cosmo;
+
+typedef struct nu_halo {
+    double M_h;      /* halo mass, Msun (>= 0; 0 means no halo)                */
+    double c;        /* concentration r200 / r_s (> 0)                          */
+    double z0;       /* observation redshift; only 0 is supported              */
+    int xi_kind;     /* NU_XI_*                                                */
+    int kappa_kind;  /* NU_KAPPA_*                                             */
+    double xi_p[3];
+    double kappa_p[3];
+} nu_halo;
+
+typedef struct nu_relic {
+    double m_eV;     /* relic mass, eV (> 0)                                   */
+    int f_kind;      /* NU_F_*                                                 */
+    int reserved;
+    double f_p[2];
+} nu_relic;
+
+typedef struct nu_pgrid {
+    int n_q;         /* momentum nodes, log-spaced on [q_min, q_max] (>= 2);
+                        trapezoid weights in ln q                              */
+    int n_mu;        /* Gauss-Legendre nodes for mu on [-1, 1] (>= 1)          */
+    double q_min;    /* > 0, units of k_B T0                                   */
+    double q_max;    /* > q_min                                                */
+} nu_pgrid;
+
+/* Device allocator hooks: alloc returns a device pointer (NULL on failure),
+ * free releases one.  With alloc == NULL the library calls cudaMalloc/cudaFree. */
+typedef void* (*nu_alloc_fn)(size_t bytes, void* ctx);
+typedef void  (*nu_free_fn)(void* ptr, size_t bytes, void* ctx);
+
+typedef struct nu_opts {
+    int n_steps;         /* RK4 steps from z0 to z_end (1 .. NU_MAX_STEPS)       */
+    int precision;       /* NU_FP64 or NU_MIXED                                   */
+    double z_end;        /* end of the backward integration; <= 0 -> the paper's z_i */
+    int radii_unit;      /* NU_RADII_*                                            */
+    int block;           /* threads per CTA: 0 (default 256) or 64..512, multiple of 32 */
+    int tpt;             /* trajectories per thread: 0 (default 1), 1 or 2       */
+    int flags;           /* NU_FLAG_*                                             */
+    nu_alloc_fn alloc;
+    nu_free_fn free;
+    void* alloc_ctx;
+    void* stream;        /* cudaStream_t used for uploads during create           */
+} nu_opts;
+
+#define NU_MAX_STEPS 3000  /* the per-step coefficient table lives in shared memory */
+
+typedef struct nu_profile nu_profile;
+typedef struct nu_batch nu_batch;
+
+/* Host-side summary of a request: derived halo quantities (Sec. II.B) and
+ * sizes.  Filled by nu_profile_plan without touching the GPU. */
+typedef struct nu_plan_info {
+    double R_kpc;            /* comoving radius of the collapsing region      */
+    double r200_kpc;         /* physical virial radius                        */
+    double r_s_kpc;          /* NFW scale radius                              */
+    double z_i;              /* onset redshift, (1+z_i) = 200^(1/3) (1+z0)    */
+    double Ic;               /* ln(1+c) - c/(1+c)                             */
+    double rho_bar0;         /* mean matter density today, Msun/kpc^3         */
+    double z_end;            /* resolved end redshift                         */
+    long long n_traj;        /* n_radii * n_q * n_mu                          */
+    long long traj_steps;    /* n_traj * n_steps                              */
+    long long device_bytes;  /* device memory create() will allocate          */
+    int n_tiles;             /* work tiles of one run                         */
+    int tile;                /* trajectories per tile (block * tpt)           */
+} nu_plan_info;
+
+/* Fill *info for the request (validation + Sec. II.B derivation + sizing).
+ * Needs no GPU.  Errors: NU_EINVAL for out-of-range inputs, NU_ENOTSUP for
+ * z0 != 0 or n_steps > NU_MAX_STEPS. */
+NU_API int nu_profile_plan(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
+                    const double* radii, int n_radii, const nu_pgrid* p_grid,
+                    const nu_opts* opts, nu_plan_info* info);
+
+/* Create a profile request (Sec. II.B-II.D).  Validates, derives the halo in
+ * FP64 on the host, builds the per-step coefficient table (background H(z),
+ * growth xi(z), coupling kappa(z) at every RK stage), the q and mu nodes and
+ * weights and the background normalisation, allocates the device buffers
+ * (through opts->alloc when given) and uploads them on opts->stream.
+ * radii: n_radii values > 0 in opts->radii_unit.  *out is set only on success.
+ * Errors: NU_EINVAL, NU_ENOTSUP, NU_ENOMEM, NU_ECUDA. */
+NU_API int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
+                      const double* radii, int n_radii, const nu_pgrid* p_grid,
+                      const nu_opts* opts, nu_profile** out);
+
+/* Enqueue one evaluation of Eq. localdensity / nbar for every radius on
+ * `stream` (asynchronous): backward RK4 trajectories (Eq. eoms with the
+ * App. A gradient), Liouville map, f, and the quadrature reduction, in one
+ * persistent kernel.  Re-running is idempotent.  Errors: NU_EINVAL (NULL
+ * handle), NU_ECUDA (launch failure). */
+NU_API int nu_profile_run(nu_profile* h, void* stream);
+
+/* Wait for the last run of `h` and copy n/nbar (and, if err_est != NULL, an
+ * estimate of the relative quadrature error of each value: the difference to
+ * the same sum on a grid with every other q node, divided by 3) into host
+ * arrays of n_radii doubles.  Errors: NU_EBUSY (never run), NU_EINVAL
+ * (n_radii mismatch), NU_EDEVICE (non-finite sum), NU_ECUDA. */
+NU_API int nu_profile_result(nu_profile* h, double* n_over_nbar, double* err_est, int n_radii);
+
+/* Copy the final momenta q_i (units of k_B T0) of every trajectory of the last
+ * run, ordered [radius][q][mu], into a host array of n values
+ * (n = n_radii * n_q * n_mu).  Needs NU_FLAG_KEEP_QI at create; this is the
+ * phase-space integrand of Sec. III (Fig. 3).  Errors: NU_EINVAL, NU_EBUSY,
+ * NU_ECUDA. */
+NU_API int nu_profile_qi(nu_profile* h, double* qi, long long n);
+
+/* Plan numbers of an existing handle. */
+NU_API int nu_profile_info(const nu_profile* h, nu_plan_info* info);
+
+/* Release a handle and its device memory (waits for its last run). NULL-safe. */
+NU_API void nu_profile_destroy(nu_profile* h);
+
+/* Batch several requests into ONE persistent launch (uneven halos x radii x
+ * grids drained from a shared work list).  All handles must have the same
+ * precision and tile shape; each keeps its own outputs, read with
+ * nu_profile_result.  The handles must outlive the batch.  opts may be NULL;
+ * opts->flags & NU_FLAG_GRAPH captures the launch in a CUDA graph at the
+ * first run and replays it afterwards.  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
+NU_API int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch** out);
+NU_API int nu_batch_run(nu_batch* b, void* stream);
+NU_API void nu_batch_destroy(nu_batch* b);
+
+/* Launch counters: kernels launched by the library since load (all handles). */
+NU_API long long nu_kernel_launches(void);
+
+NU_API const char* nu_strerror(int code);
+NU_API int nu_version(void);   /* 10000*major + 100*minor + patch */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUPROF_H */

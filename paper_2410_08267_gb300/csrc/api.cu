@@ -1,0 +1,568 @@
+// C-ABI of the relic-overdensity library: request handles, batches and the
+// host side of every launch.  See include/nuprof.h for the contract of each
+// entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "nuprof_internal.h"
+
+using namespace nuprof;
+
+namespace nuprof {
+long long launches();
+}
+
+namespace {
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Device memory through the caller's allocator or cudaMalloc.
+struct DeviceBlock {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    nu_alloc_fn alloc = nullptr;
+    nu_free_fn free = nullptr;
+    void* ctx = nullptr;
+
+    int allocate(size_t n, const nu_opts& o)
+    {
+        alloc = o.alloc;
+        free = o.free;
+        ctx = o.alloc_ctx;
+        bytes = n;
+        if (alloc) {
+            ptr = alloc(n, ctx);
+            return ptr ? NU_OK : NU_ENOMEM;
+        }
+        if (cudaMalloc(&ptr, n) != cudaSuccess) {
+            cudaGetLastError();
+            ptr = nullptr;
+            return NU_ENOMEM;
+        }
+        return NU_OK;
+    }
+    void release()
+    {
+        if (!ptr) return;
+        if (alloc) {
+            if (free) free(ptr, bytes, ctx);
+        } else {
+            cudaFree(ptr);
+        }
+        ptr = nullptr;
+    }
+};
+
+// An event shared by every handle that took part in one launch.
+struct RunEvent {
+    cudaEvent_t ev = nullptr;
+    RunEvent() { cudaEventCreateWithFlags(&ev, cudaEventDisableTiming); }
+    ~RunEvent()
+    {
+        if (ev) cudaEventDestroy(ev);
+    }
+};
+
+int sm_count()
+{
+    static std::atomic<int> cached{0};
+    int v = cached.load();
+    if (v) return v;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cached.store(v);
+    return v;
+}
+
+int persistent_grid(int precision, int tpt, int block, size_t smem, int n_tiles, int* grid)
+{
+    int per_sm = 0;
+    const int rc = max_ctas_per_sm(precision, tpt, block, smem, &per_sm);
+    if (rc != NU_OK) return rc;
+    const int sms = sm_count();
+    if (per_sm < 1 || sms < 1) return NU_ECUDA;
+    *grid = std::max(1, std::min(n_tiles, per_sm * sms));
+    return NU_OK;
+}
+
+}  // namespace
+
+struct nu_profile {
+    nu_cosmo cosmo;
+    nu_halo halo;
+    nu_relic relic;
+    nu_pgrid grid;
+    nu_opts opts;
+    Derived d;
+    nu_plan_info info;
+    int n_radii = 0;
+    int tiles_per_seg = 0;
+    int n_tiles = 0;
+    size_t smem = 0;
+    DeviceBlock mem;
+    DevProblem hdp;                 // host copy (device pointers inside)
+    DevProblem* d_prob = nullptr;
+    int* d_prefix = nullptr;
+    unsigned* d_ctrl = nullptr;     // [0] tile counter, [1] status
+    std::shared_ptr<RunEvent> last;
+};
+
+struct nu_batch {
+    std::vector<nu_profile*> hs;
+    int precision = NU_MIXED, tpt = 1, block = 256;
+    int n_tiles = 0;
+    size_t smem = 0;
+    int grid = 0;
+    DeviceBlock mem;
+    DevProblem* d_probs = nullptr;
+    int* d_prefix = nullptr;
+    unsigned* d_ctrl = nullptr;
+    bool use_graph = false;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    std::shared_ptr<RunEvent> ev;
+};
+
+namespace {
+
+int plan_common(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
+                const double* radii, int n_radii, const nu_pgrid* grid, const nu_opts* opts_in,
+                nu_opts& o, Derived& d, nu_plan_info& info, int& tiles_per_seg)
+{
+    resolve_opts(opts_in, o);
+    int rc = validate(cosmo, halo, relic, radii, n_radii, grid, &o);
+    if (rc != NU_OK) return rc;
+    rc = derive(*cosmo, *halo, o, d);
+    if (rc != NU_OK) return rc;
+    const long long seg = (long long)grid->n_q * grid->n_mu;
+    const int tile = o.block * o.tpt;
+    tiles_per_seg = (int)((seg + tile - 1) / tile);
+    std::memset(&info, 0, sizeof(info));
+    info.R_kpc = d.R;
+    info.r200_kpc = d.r200;
+    info.r_s_kpc = d.r_s;
+    info.z_i = d.z_i;
+    info.Ic = d.Ic;
+    info.rho_bar0 = d.rho_bar0;
+    info.z_end = d.z_end;
+    info.n_traj = seg * n_radii;
+    info.traj_steps = info.n_traj * o.n_steps;
+    info.device_bytes = device_bytes(o.precision, o.n_steps, n_radii, grid->n_q, grid->n_mu,
+                                     tiles_per_seg, (o.flags & NU_FLAG_KEEP_QI) != 0);
+    const long long nt = (long long)tiles_per_seg * n_radii;
+    if (nt > (1LL << 30)) return NU_EINVAL;
+    info.n_tiles = (int)nt;
+    info.tile = tile;
+    return NU_OK;
+}
+
+// Append `n` values of type T (converted from double) to a staging buffer at offset off.
+template <typename T>
+void put(std::vector<unsigned char>& buf, size_t off, const double* v, size_t n)
+{
+    T* p = reinterpret_cast<T*>(buf.data() + off);
+    for (size_t i = 0; i < n; ++i) p[i] = (T)v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+int nu_version(void) { return NU_VERSION_MAJOR * 10000 + NU_VERSION_MINOR * 100 + NU_VERSION_PATCH; }
+
+const char* nu_strerror(int code)
+{
+    switch (code) {
+    case NU_OK: return "ok";
+    case NU_EINVAL: return "invalid argument";
+    case NU_ENOMEM: return "out of memory";
+    case NU_ECUDA: return "CUDA runtime error";
+    case NU_EBUSY: return "no run has been enqueued";
+    case NU_ETIMEDOUT: return "timed out";
+    case NU_EDEVICE: return "device reported a non-finite result";
+    case NU_ENOTSUP: return "unsupported combination";
+    case NU_ECANCELED: return "cancelled";
+    case NU_EAGAIN: return "not finished yet";
+    default: return "unknown error";
+    }
+}
+
+long long nu_kernel_launches(void) { return nuprof::launches(); }
+
+int nu_profile_plan(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
+                    const double* radii, int n_radii, const nu_pgrid* p_grid,
+                    const nu_opts* opts, nu_plan_info* info)
+{
+    if (!info) return NU_EINVAL;
+    nu_opts o;
+    Derived d;
+    nu_plan_info tmp;
+    int tps = 0;
+    const int rc = plan_common(cosmo, halo, relic, radii, n_radii, p_grid, opts, o, d, tmp, tps);
+    if (rc != NU_OK) return rc;
+    *info = tmp;
+    return NU_OK;
+}
+
+int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
+                      const double* radii, int n_radii, const nu_pgrid* p_grid,
+                      const nu_opts* opts, nu_profile** out)
+{
+    if (!out) return NU_EINVAL;
+    nu_opts o;
+    Derived d;
+    nu_plan_info info;
+    int tps = 0;
+    int rc = plan_common(cosmo, halo, relic, radii, n_radii, p_grid, opts, o, d, info, tps);
+    if (rc != NU_OK) return rc;
+
+    std::unique_ptr<nu_profile> h(new (std::nothrow) nu_profile());
+    if (!h) return NU_ENOMEM;
+    h->cosmo = *cosmo;
+    h->halo = *halo;
+    h->relic = *relic;
+    h->grid = *p_grid;
+    h->opts = o;
+    h->d = d;
+    h->info = info;
+    h->n_radii = n_radii;
+    h->tiles_per_seg = tps;
+    h->n_tiles = info.n_tiles;
+    h->smem = coef_smem_bytes(o.precision, o.n_steps);
+
+    // ---- host tables (FP64) ----
+    const int nq = p_grid->n_q, nmu = p_grid->n_mu, N = o.n_steps;
+    std::vector<double> coef, q, wq, wqc, mu, wmu;
+    coef_table(*cosmo, *halo, d, N, coef);
+    log_nodes(nq, p_grid->q_min, p_grid->q_max, q, wq, wqc);
+    gauss_legendre(nmu, mu, wmu);
+    const double kT0 = kKB * cosmo->T0_K;                 // eV
+    std::vector<double> v0(nq), smu(nmu), x0(n_radii);
+    for (int j = 0; j < nq; ++j) v0[j] = kC * q[j] * kT0 / relic->m_eV;   // Sec. II.C: P0 = m v0
+    for (int k = 0; k < nmu; ++k) smu[k] = std::sqrt((1.0 - mu[k]) * (1.0 + mu[k]));
+    for (int i = 0; i < n_radii; ++i)
+        x0[i] = o.radii_unit == NU_RADII_R200 ? radii[i] * d.r200 : radii[i];
+    double nb = 0.0, nbc = 0.0;                            // background, same grid
+    for (int j = 0; j < nq; ++j) {
+        const double f = relic_f(*relic, q[j]);
+        nb += wq[j] * f;
+        nbc += wqc[j] * f;
+    }
+
+    // ---- device layout ----
+    const bool fp64 = o.precision == NU_FP64;
+    const size_t sz = fp64 ? sizeof(double) : sizeof(float);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
+    const size_t o_ctrl = carve(4 * sizeof(unsigned));
+    const size_t o_prob = carve(sizeof(DevProblem));
+    const size_t o_pref = carve(2 * sizeof(int));
+    const size_t o_coef = carve((size_t)N * C_COUNT * sz);
+    const size_t o_x0 = carve((size_t)n_radii * sz);
+    const size_t o_v0 = carve((size_t)nq * sz);
+    const size_t o_mu = carve((size_t)nmu * sz);
+    const size_t o_smu = carve((size_t)nmu * sz);
+    const size_t o_wq = carve((size_t)nq * sizeof(double));
+    const size_t o_wqc = carve((size_t)nq * sizeof(double));
+    const size_t o_wmu = carve((size_t)nmu * sizeof(double));
+    const size_t upload_end = off;                         // everything above is uploaded
+    const size_t o_part = carve((size_t)n_radii * tps * 2 * sizeof(double));
+    const size_t o_cnt = carve((size_t)n_radii * sizeof(unsigned));
+    const size_t o_out = carve((size_t)n_radii * sizeof(double));
+    const size_t o_err = carve((size_t)n_radii * sizeof(double));
+    const bool keep_qi = (o.flags & NU_FLAG_KEEP_QI) != 0;
+    const size_t o_qi = keep_qi ? carve((size_t)n_radii * nq * nmu * sizeof(float)) : 0;
+    const size_t total = off;
+
+    rc = h->mem.allocate(total, o);
+    if (rc != NU_OK) return rc;
+    unsigned char* base = static_cast<unsigned char*>(h->mem.ptr);
+
+    DevProblem& P = h->hdp;
+    std::memset(&P, 0, sizeof(P));
+    P.coef = base + o_coef;
+    P.x0 = base + o_x0;
+    P.v0 = base + o_v0;
+    P.mu = base + o_mu;
+    P.smu = base + o_smu;
+    P.wq = reinterpret_cast<const double*>(base + o_wq);
+    P.wqc = reinterpret_cast<const double*>(base + o_wqc);
+    P.wmu = reinterpret_cast<const double*>(base + o_wmu);
+    P.partials = reinterpret_cast<double*>(base + o_part);
+    P.seg_count = reinterpret_cast<unsigned*>(base + o_cnt);
+    P.out = reinterpret_cast<double*>(base + o_out);
+    P.err = reinterpret_cast<double*>(base + o_err);
+    P.qi = keep_qi ? reinterpret_cast<float*>(base + o_qi) : nullptr;
+    P.status = reinterpret_cast<int*>(base + o_ctrl + sizeof(unsigned));
+    P.q_scale = relic->m_eV / (kC * kT0);                 // Liouville map: q_i = m |v| / (c k_B T0)
+    P.inv_norm = 1.0 / (2.0 * nb);
+    P.inv_norm_c = 1.0 / (2.0 * nbc);
+    P.invIc = 1.0 / d.Ic;
+    P.invR3 = d.R > 0.0 ? 1.0 / (d.R * d.R * d.R) : 0.0;
+    P.R2 = d.R * d.R;
+    P.f_p0 = relic->f_p[0];
+    P.f_kind = relic->f_kind;
+    P.n_radii = n_radii;
+    P.n_q = nq;
+    P.n_mu = nmu;
+    P.n_steps = N;
+    P.tiles_per_seg = tps;
+    P.tile = o.block * o.tpt;
+    P.precision = o.precision;
+
+    std::vector<unsigned char> stage(upload_end, 0);
+    std::memcpy(stage.data() + o_prob, &P, sizeof(P));
+    const int prefix[2] = {0, h->n_tiles};
+    std::memcpy(stage.data() + o_pref, prefix, sizeof(prefix));
+    if (fp64) {
+        put<double>(stage, o_coef, coef.data(), coef.size());
+        put<double>(stage, o_x0, x0.data(), n_radii);
+        put<double>(stage, o_v0, v0.data(), nq);
+        put<double>(stage, o_mu, mu.data(), nmu);
+        put<double>(stage, o_smu, smu.data(), nmu);
+    } else {
+        put<float>(stage, o_coef, coef.data(), coef.size());
+        put<float>(stage, o_x0, x0.data(), n_radii);
+        put<float>(stage, o_v0, v0.data(), nq);
+        put<float>(stage, o_mu, mu.data(), nmu);
+        put<float>(stage, o_smu, smu.data(), nmu);
+    }
+    put<double>(stage, o_wq, wq.data(), nq);
+    put<double>(stage, o_wqc, wqc.data(), nq);
+    put<double>(stage, o_wmu, wmu.data(), nmu);
+
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
+    if (cudaMemcpyAsync(base, stage.data(), upload_end, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(base + o_cnt, 0, (size_t)n_radii * sizeof(unsigned), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {   // the staging buffer is pageable and local
+        cudaGetLastError();
+        h->mem.release();
+        return NU_ECUDA;
+    }
+    h->d_prob = reinterpret_cast<DevProblem*>(base + o_prob);
+    h->d_prefix = reinterpret_cast<int*>(base + o_pref);
+    h->d_ctrl = reinterpret_cast<unsigned*>(base + o_ctrl);
+    *out = h.release();
+    return NU_OK;
+}
+
+int nu_profile_run(nu_profile* h, void* stream)
+{
+    if (!h) return NU_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int grid = 0;
+    int rc = persistent_grid(h->opts.precision, h->opts.tpt, h->opts.block, h->smem, h->n_tiles, &grid);
+    if (rc != NU_OK) return rc;
+    if (cudaMemsetAsync(h->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    rc = launch_traj(h->opts.precision, h->opts.tpt, h->opts.block, grid, h->smem, h->d_prob,
+                     h->d_prefix, 1, h->n_tiles, h->d_ctrl, stream);
+    if (rc != NU_OK) return rc;
+    auto ev = std::make_shared<RunEvent>();
+    if (!ev->ev || cudaEventRecord(ev->ev, s) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    h->last = ev;
+    return NU_OK;
+}
+
+int nu_profile_result(nu_profile* h, double* n_over_nbar, double* err_est, int n_radii)
+{
+    if (!h || !n_over_nbar) return NU_EINVAL;
+    if (n_radii != h->n_radii) return NU_EINVAL;
+    if (!h->last) return NU_EBUSY;
+    if (cudaEventSynchronize(h->last->ev) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    // out and err are adjacent in the device layout: one copy brings both back
+    std::vector<double> tmp((size_t)2 * n_radii);
+    const size_t stride = (size_t)(reinterpret_cast<const char*>(h->hdp.err) -
+                                   reinterpret_cast<const char*>(h->hdp.out));
+    if (cudaMemcpy2D(tmp.data(), n_radii * sizeof(double), h->hdp.out, stride,
+                     n_radii * sizeof(double), err_est ? 2 : 1, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    for (int i = 0; i < n_radii; ++i)
+        if (!std::isfinite(tmp[i])) return NU_EDEVICE;
+    std::memcpy(n_over_nbar, tmp.data(), n_radii * sizeof(double));
+    if (err_est) std::memcpy(err_est, tmp.data() + n_radii, n_radii * sizeof(double));
+    return NU_OK;
+}
+
+int nu_profile_qi(nu_profile* h, double* qi, long long n)
+{
+    if (!h || !qi) return NU_EINVAL;
+    if (!h->hdp.qi) return NU_EINVAL;
+    const long long total = (long long)h->n_radii * h->grid.n_q * h->grid.n_mu;
+    if (n != total) return NU_EINVAL;
+    if (!h->last) return NU_EBUSY;
+    if (cudaEventSynchronize(h->last->ev) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    std::vector<float> tmp((size_t)total);
+    if (cudaMemcpy(tmp.data(), h->hdp.qi, total * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    for (long long i = 0; i < total; ++i) qi[i] = tmp[(size_t)i];
+    return NU_OK;
+}
+
+int nu_profile_info(const nu_profile* h, nu_plan_info* info)
+{
+    if (!h || !info) return NU_EINVAL;
+    *info = h->info;
+    return NU_OK;
+}
+
+void nu_profile_destroy(nu_profile* h)
+{
+    if (!h) return;
+    if (h->last) cudaEventSynchronize(h->last->ev);
+    h->last.reset();
+    h->mem.release();
+    delete h;
+}
+
+int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch** out)
+{
+    if (!hs || n < 1 || !out) return NU_EINVAL;
+    std::unique_ptr<nu_batch> b(new (std::nothrow) nu_batch());
+    if (!b) return NU_ENOMEM;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) return NU_EINVAL;
+        const nu_opts& o = hs[i]->opts;
+        if (i == 0) {
+            b->precision = o.precision;
+            b->tpt = o.tpt;
+            b->block = o.block;
+        } else if (o.precision != b->precision || o.tpt != b->tpt || o.block != b->block) {
+            return NU_EINVAL;
+        }
+        b->smem = std::max(b->smem, hs[i]->smem);
+        b->hs.push_back(hs[i]);
+    }
+    std::vector<int> prefix(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        const long long next = (long long)prefix[i] + hs[i]->n_tiles;
+        if (next > (1LL << 30)) return NU_EINVAL;
+        prefix[i + 1] = (int)next;
+    }
+    b->n_tiles = prefix[n];
+
+    nu_opts o;
+    resolve_opts(opts, o);
+    if (opts) b->use_graph = (opts->flags & NU_FLAG_GRAPH) != 0;
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
+    const size_t o_ctrl = carve(4 * sizeof(unsigned));
+    const size_t o_probs = carve((size_t)n * sizeof(DevProblem));
+    const size_t o_pref = carve((size_t)(n + 1) * sizeof(int));
+    int rc = b->mem.allocate(off, o);
+    if (rc != NU_OK) return rc;
+    std::vector<unsigned char> stage(off, 0);
+    for (int i = 0; i < n; ++i)
+        std::memcpy(stage.data() + o_probs + i * sizeof(DevProblem), &hs[i]->hdp, sizeof(DevProblem));
+    std::memcpy(stage.data() + o_pref, prefix.data(), (n + 1) * sizeof(int));
+    unsigned char* base = static_cast<unsigned char*>(b->mem.ptr);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
+    if (cudaMemcpyAsync(base, stage.data(), off, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        b->mem.release();
+        return NU_ECUDA;
+    }
+    b->d_ctrl = reinterpret_cast<unsigned*>(base + o_ctrl);
+    b->d_probs = reinterpret_cast<DevProblem*>(base + o_probs);
+    b->d_prefix = reinterpret_cast<int*>(base + o_pref);
+    rc = persistent_grid(b->precision, b->tpt, b->block, b->smem, b->n_tiles, &b->grid);
+    if (rc != NU_OK) {
+        b->mem.release();
+        return rc;
+    }
+    b->ev = std::make_shared<RunEvent>();
+    *out = b.release();
+    return NU_OK;
+}
+
+static int batch_enqueue(nu_batch* b, cudaStream_t s)
+{
+    if (cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return NU_ECUDA;
+    return launch_traj(b->precision, b->tpt, b->block, b->grid, b->smem, b->d_probs, b->d_prefix,
+                       (int)b->hs.size(), b->n_tiles, b->d_ctrl, s);
+}
+
+int nu_batch_run(nu_batch* b, void* stream)
+{
+    if (!b) return NU_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int rc = NU_OK;
+    if (b->use_graph) {
+        if (!b->exec) {
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                cudaGetLastError();
+                return NU_ECUDA;
+            }
+            rc = batch_enqueue(b, s);
+            const cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (rc != NU_OK || e != cudaSuccess) {
+                cudaGetLastError();
+                if (g) cudaGraphDestroy(g);
+                return NU_ECUDA;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                cudaGetLastError();
+                b->exec = nullptr;
+                return NU_ECUDA;
+            }
+        }
+        if (cudaGraphLaunch(b->exec, s) != cudaSuccess) {
+            cudaGetLastError();
+            return NU_ECUDA;
+        }
+        count_launch();
+    } else {
+        rc = batch_enqueue(b, s);
+        if (rc != NU_OK) {
+            cudaGetLastError();
+            return rc;
+        }
+    }
+    auto ev = std::make_shared<RunEvent>();
+    if (!ev->ev || cudaEventRecord(ev->ev, s) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    b->ev = ev;
+    for (nu_profile* h : b->hs) h->last = ev;
+    return NU_OK;
+}
+
+void nu_batch_destroy(nu_batch* b)
+{
+    if (!b) return;
+    if (b->ev && b->ev->ev) cudaEventSynchronize(b->ev->ev);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->mem.release();
+    delete b;
+}
+
+}  // extern "C"

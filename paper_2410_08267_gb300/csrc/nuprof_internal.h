@@ -1,0 +1,100 @@
+// Internal declarations of the relic-overdensity library (not part of the C-ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "nuprof.h"
+
+namespace nuprof {
+
+// Physical constants (kpc, km/s, Msun, eV).
+constexpr double kG = 4.30091727e-6;      // kpc (km/s)^2 / Msun
+constexpr double kC = 299792.458;         // km/s
+constexpr double kKB = 8.617333262e-5;    // eV / K
+constexpr double kPi = 3.14159265358979323846;
+
+// Entries of the per-step coefficient table (one RK4 step = 16 values).
+// With h = ln(1+z_end)/N, stage redshifts z_a, z_m, z_b at u = -n h, -(n+1/2) h,
+// -(n+1) h, A(z) = (1+z)^2/H, B(z) = 1/H and F(z) = G kappa (1+z) xi M_h:
+enum CoefSlot {
+    C_MA1 = 0,   // -(h/2) A(z_a)        X2 = x + C_MA1 v
+    C_MA2,       // -(h/2) A(z_m)        X3 = x + C_MA2 V2
+    C_MA3,       // -h A(z_m)            X4 = x + C_MA3 V3
+    C_B1,        // (h/2) B F (z_a)      V2 = v + C_B1 m1 x
+    C_B2,        // (h/2) B F (z_m)      V3 = v + C_B2 m2 X2
+    C_B3,        // h B F (z_m)          V4 = v + C_B3 m3 X3
+    C_B4,        // (h/6) B F (z_b)
+    C_W0,        // -(h/6) A(z_a)        x' = x + W0 v + W1 (V2+V3) + W2 V4
+    C_W1,        // -(h/3) A(z_m)
+    C_W2,        // -(h/6) A(z_b)
+    C_S0,        // 1/((1+z_a) r_s)      NFW argument scale
+    C_S1,        // 1/((1+z_m) r_s)
+    C_S2,        // 1/((1+z_b) r_s)
+    C_Q0,        // (r200 (1+z_a))^2     squared comoving edge of the NFW part
+    C_Q1,
+    C_Q2,
+    C_COUNT
+};
+static_assert(C_COUNT == 16, "coefficient table layout");
+
+// Halo and background quantities derived on the host in FP64 (Sec. II.B).
+struct Derived {
+    double H0, rho_bar0, R, z_i, r200, r_s, Ic;
+    double xi_zs, xi_ze;   // growth window used by NU_XI_LINEAR
+    double z_end;          // resolved end of the backward integration
+};
+
+int validate(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
+             const double* radii, int n_radii, const nu_pgrid* grid, const nu_opts* opts);
+int derive(const nu_cosmo& cosmo, const nu_halo& halo, const nu_opts& opts, Derived& d);
+double hubble(const nu_cosmo& cosmo, const Derived& d, double z);
+double growth_xi(const nu_halo& halo, const Derived& d, double z);
+double coupling_kappa(const nu_halo& halo, double z);
+double relic_f(const nu_relic& relic, double q);
+void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps,
+                std::vector<double>& table);
+void log_nodes(int n, double q_min, double q_max, std::vector<double>& q,
+               std::vector<double>& wl, std::vector<double>& wl_coarse);
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+void resolve_opts(const nu_opts* in, nu_opts& out);
+long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_mu,
+                       int tiles_per_seg, bool keep_qi);
+
+// Device-visible description of one request (POD, lives in device memory).
+struct DevProblem {
+    const void* coef;       // [n_steps][16] float (mixed) or double (fp64)
+    const void* x0;         // [n_radii] start radius, kpc
+    const void* v0;         // [n_q] start speed, km/s
+    const void* mu;         // [n_mu] cos psi
+    const void* smu;        // [n_mu] sin psi
+    const double* wq;       // [n_q] trapezoid-in-ln q weight x q^3
+    const double* wqc;      // [n_q] same on every other node (error estimate)
+    const double* wmu;      // [n_mu] Gauss-Legendre weights
+    double* partials;       // [n_radii][tiles_per_seg][2] tile sums
+    unsigned* seg_count;    // [n_radii] tiles finished (reset by the finisher)
+    double* out;            // [n_radii] n/nbar
+    double* err;            // [n_radii] relative quadrature-error estimate
+    float* qi;              // [n_radii][n_q][n_mu] final q (optional)
+    int* status;            // bit 0: non-finite sum
+    double q_scale;         // q_i = |v| * q_scale
+    double inv_norm;        // 1 / (2 sum_j wq_j f(q_j))
+    double inv_norm_c;      // same with wqc
+    double invIc, invR3, R2;
+    double f_p0;
+    int f_kind;
+    int n_radii, n_q, n_mu, n_steps;
+    int tiles_per_seg, tile;
+    int precision;
+};
+
+// Kernel launch helpers (traj_kernel.cu).
+int launch_traj(int precision, int tpt, int block, int grid, size_t smem_bytes,
+                const DevProblem* d_probs, const int* d_tile_prefix, int n_probs, int n_tiles,
+                unsigned* d_tile_counter, void* stream);
+int max_ctas_per_sm(int precision, int tpt, int block, size_t smem_bytes, int* out);
+size_t coef_smem_bytes(int precision, int n_steps);
+void count_launch();
+
+}  // namespace nuprof

@@ -1,0 +1,386 @@
+// Persistent trajectory kernel for relic overdensity profiles (sm_103a).
+//
+// One thread integrates TPT trajectories (one per (radius, |P0|, mu) triple,
+// Sec. II.C) backward from z0 = 0 to z_end with classical RK4 in u = ln a
+// (Eq. eoms), the force being the closed-form gradient of the compensated,
+// growing NFW halo (App. A).  The state (x, y, vx, vy) stays in registers for
+// the whole integration; the per-step coefficients (background, growth,
+// coupling at the three RK stage times, built in FP64 on the host) are staged
+// once per request into shared memory and read as broadcast vector loads.
+// At the end the Liouville map f0 = f_init(P_i) (Sec. II.C) and the weight of
+// the trajectory in Eq. localdensity are applied, and the tile's sum is formed
+// by a warp-shuffle + shared-memory tree.  Tile sums land in a per-request
+// array; the CTA that completes the last tile of a radius adds them in tile
+// order (so every result is bitwise independent of scheduling and of what
+// else shares the launch) and writes n/nbar.
+//
+// Work distribution: CTAs of a persistent grid pull tile indices from one
+// atomic counter; a tile is `tile` consecutive trajectories of one radius of
+// one request, so uneven batches of requests share one launch.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+
+#include "nuprof_internal.h"
+
+namespace nuprof {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// Force evaluation: m = Mhat(r, z) / r^3, so that gradPhi / F = m * (x, y).
+//   Mhat = I(r/(r_s (1+z))) / I(c) - (r/R)^3   for r < r200 (1+z)
+//        = 1 - (r/R)^3                         for r < R
+//        = 0                                   otherwise          (App. A)
+// which gives m = sel / r^3 - 1/R^3 with sel = I/I(c) inside the NFW edge and
+// 1 in the shell, and m = 0 beyond R.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float rsqrt_approx(float v)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// I(y) = ln(1+y) - y/(1+y) (Eq. nfw) in FP32.  Below y = 0.15 the two terms
+// cancel, so the Taylor series I/y^2 = sum_k (-1)^k (k+1)/(k+2) y^k is used
+// through k = 8 (truncation below 1e-7 relative there).
+__device__ __forceinline__ float nfw_I(float y)
+{
+    if (y < 0.15f) {
+        float p = 9.0f / 10.0f;
+        p = fmaf(p, y, -8.0f / 9.0f);
+        p = fmaf(p, y, 7.0f / 8.0f);
+        p = fmaf(p, y, -6.0f / 7.0f);
+        p = fmaf(p, y, 5.0f / 6.0f);
+        p = fmaf(p, y, -4.0f / 5.0f);
+        p = fmaf(p, y, 3.0f / 4.0f);
+        p = fmaf(p, y, -2.0f / 3.0f);
+        p = fmaf(p, y, 0.5f);
+        return (y * y) * p;
+    }
+    return log1pf(y) - __fdividef(y, 1.0f + y);
+}
+
+// Same in FP64: series through k = 11 below y = 0.02.
+__device__ __forceinline__ double nfw_I(double y)
+{
+    if (y < 0.02) {
+        double p = 0.0;
+        for (int k = 11; k >= 0; --k) {
+            const double c = (double)(k + 1) / (double)(k + 2);
+            p = fma(p, y, (k & 1) ? -c : c);
+        }
+        return (y * y) * p;
+    }
+    return log1p(y) - y / (1.0 + y);
+}
+
+struct HaloF32 { float invIc, invR3, R2; };
+struct HaloF64 { double invIc, invR3, R2; };
+
+__device__ __forceinline__ float accel_m(float x, float y, float S, float Q, const HaloF32& hc)
+{
+    const float r2 = fmaxf(fmaf(x, x, y * y), 1e-20f);   // r -> 0 guard (below 1e-10 kpc)
+    const float rinv = rsqrt_approx(r2);
+    const float rinv3 = rinv * rinv * rinv;
+    const float ys = (r2 * rinv) * S;
+    const float sel = (r2 < Q) ? nfw_I(ys) * hc.invIc : 1.0f;
+    const float m = fmaf(sel, rinv3, -hc.invR3);
+    return (r2 < hc.R2) ? m : 0.0f;
+}
+
+__device__ __forceinline__ double accel_m(double x, double y, double S, double Q, const HaloF64& hc)
+{
+    const double r2 = fmax(fma(x, x, y * y), 1e-200);
+    const double rinv = rsqrt(r2);
+    const double rinv3 = rinv * rinv * rinv;
+    const double ys = (r2 * rinv) * S;
+    const double sel = (r2 < Q) ? nfw_I(ys) * hc.invIc : 1.0;
+    const double m = fma(sel, rinv3, -hc.invR3);
+    return (r2 < hc.R2) ? m : 0.0;
+}
+
+template <typename T> struct PrecTraits;
+template <> struct PrecTraits<float> {
+    using Halo = HaloF32;
+    static __device__ __forceinline__ Halo halo(const DevProblem& P)
+    {
+        return {(float)P.invIc, (float)P.invR3, (float)P.R2};
+    }
+};
+template <> struct PrecTraits<double> {
+    using Halo = HaloF64;
+    static __device__ __forceinline__ Halo halo(const DevProblem& P)
+    {
+        return {P.invIc, P.invR3, P.R2};
+    }
+};
+
+// Initial distribution f(q) (Sec. II.C, Sec. IV.B) in the state precision.
+__device__ __forceinline__ float relic_f_dev(int kind, float eta, float q)
+{
+    if (kind == NU_F_FREEZEIN) {
+        const float qq = fmaxf(q, 1e-30f);
+        return expf(-qq) * rsqrtf(qq);
+    }
+    return 1.0f / (1.0f + expf(q - eta));
+}
+__device__ __forceinline__ double relic_f_dev(int kind, double eta, double q)
+{
+    if (kind == NU_F_FREEZEIN) {
+        const double qq = fmax(q, 1e-300);
+        return exp(-qq) / sqrt(qq);
+    }
+    return 1.0 / (1.0 + exp(q - eta));
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One classical RK4 step of size -h for one trajectory (Eq. eoms in ln a).
+// c points at the step's 16 coefficients (see CoefSlot).
+template <typename T>
+__device__ __forceinline__ void rk4_step(T& x, T& y, T& vx, T& vy, const T* c,
+                                         const typename PrecTraits<T>::Halo& hc)
+{
+    const T m1 = accel_m(x, y, c[C_S0], c[C_Q0], hc);
+    const T p1 = c[C_B1] * m1;
+    const T X2 = x + c[C_MA1] * vx, Y2 = y + c[C_MA1] * vy;
+    const T VX2 = vx + p1 * x, VY2 = vy + p1 * y;
+
+    const T m2 = accel_m(X2, Y2, c[C_S1], c[C_Q1], hc);
+    const T p2 = c[C_B2] * m2;
+    const T X3 = x + c[C_MA2] * VX2, Y3 = y + c[C_MA2] * VY2;
+    const T VX3 = vx + p2 * X2, VY3 = vy + p2 * Y2;
+
+    const T m3 = accel_m(X3, Y3, c[C_S1], c[C_Q1], hc);
+    const T p3 = c[C_B3] * m3;
+    const T X4 = x + c[C_MA3] * VX3, Y4 = y + c[C_MA3] * VY3;
+    const T VX4 = vx + p3 * X3, VY4 = vy + p3 * Y3;
+
+    const T m4 = accel_m(X4, Y4, c[C_S2], c[C_Q2], hc);
+    const T p4 = c[C_B4] * m4;
+
+    // x' = x - (h/6) (A_a v + 2 A_m V2 + 2 A_m V3 + A_b V4)
+    const T nx = x + c[C_W0] * vx + c[C_W1] * (VX2 + VX3) + c[C_W2] * VX4;
+    const T ny = y + c[C_W0] * vy + c[C_W1] * (VY2 + VY3) + c[C_W2] * VY4;
+    // v' = v + (h/6) (BF_a m1 x + 2 BF_m m2 X2 + 2 BF_m m3 X3 + BF_b m4 X4)
+    const T p2x2 = p2 + p2;
+    const T third = T(1) / T(3);
+    const T nvx = vx + (p1 * x + p2x2 * X2 + p3 * X3) * third + p4 * X4;
+    const T nvy = vy + (p1 * y + p2x2 * Y2 + p3 * Y3) * third + p4 * Y4;
+    x = nx;
+    y = ny;
+    vx = nvx;
+    vy = nvy;
+}
+
+template <typename T, int TPT>
+__global__ void __launch_bounds__(512)
+traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_prefix,
+            int n_probs, int n_tiles, unsigned* __restrict__ tile_counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* s_coef = reinterpret_cast<T*>(smem_raw);
+    __shared__ int s_tile;
+    __shared__ int s_last;
+    __shared__ double s_red[32][2];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    int cur = -1;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
+        __syncthreads();
+        const int g = s_tile;
+        if (g >= n_tiles) break;
+
+        // request that owns global tile g: last p with tile_prefix[p] <= g
+        int lo = 0, hi = n_probs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&tile_prefix[mid]) <= g) lo = mid; else hi = mid - 1;
+        }
+        const DevProblem& P = probs[lo];
+        const int n_steps = P.n_steps;
+
+        if (lo != cur) {   // stage this request's coefficient table (uniform branch)
+            const float4* src = reinterpret_cast<const float4*>(P.coef);
+            float4* dst = reinterpret_cast<float4*>(s_coef);
+            const int n16 = (int)((size_t)n_steps * C_COUNT * sizeof(T) / 16);
+            for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(&src[i]);
+            __syncthreads();
+            cur = lo;
+        }
+
+        const int tps = P.tiles_per_seg;
+        const int lt = g - __ldg(&tile_prefix[lo]);
+        const int seg = lt / tps;
+        const int tis = lt - seg * tps;
+        const int n_mu = P.n_mu;
+        const int n_seg = P.n_q * n_mu;
+        const typename PrecTraits<T>::Halo hc = PrecTraits<T>::halo(P);
+        const T x0 = reinterpret_cast<const T*>(P.x0)[seg];
+
+        T x[TPT], y[TPT], vx[TPT], vy[TPT];
+        int tj[TPT], tk[TPT];
+        bool act[TPT];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < TPT; ++i) {
+            const int t = tis * P.tile + i * blockDim.x + threadIdx.x;
+            act[i] = t < n_seg;
+            any |= act[i];
+            const int tt = act[i] ? t : 0;
+            tj[i] = tt / n_mu;
+            tk[i] = tt - tj[i] * n_mu;
+            const T v0 = reinterpret_cast<const T*>(P.v0)[tj[i]];
+            x[i] = x0;
+            y[i] = T(0);
+            vx[i] = v0 * reinterpret_cast<const T*>(P.mu)[tk[i]];
+            vy[i] = v0 * reinterpret_cast<const T*>(P.smu)[tk[i]];
+        }
+
+        if (any) {
+            for (int n = 0; n < n_steps; ++n) {
+                T c[C_COUNT];
+                const float4* c4 = reinterpret_cast<const float4*>(s_coef + (size_t)n * C_COUNT);
+#pragma unroll
+                for (int q = 0; q < (int)(C_COUNT * sizeof(T) / 16); ++q)
+                    reinterpret_cast<float4*>(c)[q] = c4[q];
+#pragma unroll
+                for (int i = 0; i < TPT; ++i) rk4_step<T>(x[i], y[i], vx[i], vy[i], c, hc);
+            }
+        }
+
+        // Liouville map and the weight of each trajectory in Eq. localdensity
+        double acc = 0.0, accc = 0.0;
+#pragma unroll
+        for (int i = 0; i < TPT; ++i) {
+            if (!act[i]) continue;
+            const T vmag = sqrt(vx[i] * vx[i] + vy[i] * vy[i]);
+            const T qi = vmag * (T)P.q_scale;
+            const double f = (double)relic_f_dev(P.f_kind, (T)P.f_p0, qi);
+            const double wm = P.wmu[tk[i]];
+            acc += P.wq[tj[i]] * wm * f;
+            accc += P.wqc[tj[i]] * wm * f;
+            if (P.qi) {
+                const int t = tis * P.tile + i * blockDim.x + threadIdx.x;
+                P.qi[(size_t)seg * n_seg + t] = (float)qi;
+            }
+        }
+
+        // tile sum: warp shuffle, then the warps in order
+        acc = warp_sum(acc);
+        accc = warp_sum(accc);
+        if (lane == 0) {
+            s_red[warp][0] = acc;
+            s_red[warp][1] = accc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double a = lane < nwarps ? s_red[lane][0] : 0.0;
+            double ac = lane < nwarps ? s_red[lane][1] : 0.0;
+            a = warp_sum(a);
+            ac = warp_sum(ac);
+            if (lane == 0) {
+                double* part = P.partials + ((size_t)seg * tps + tis) * 2;
+                part[0] = a;
+                part[1] = ac;
+                __threadfence();
+                const unsigned prev = atomicAdd(&P.seg_count[seg], 1u);
+                s_last = (prev == (unsigned)(tps - 1));
+            }
+        }
+        __syncthreads();
+
+        if (s_last && warp == 0) {   // this CTA finished the radius: add tiles in order
+            __threadfence();
+            const double* part = P.partials + (size_t)seg * tps * 2;
+            double a = 0.0, ac = 0.0;
+            for (int i = lane; i < tps; i += 32) {
+                a += __ldcg(&part[2 * i]);
+                ac += __ldcg(&part[2 * i + 1]);
+            }
+            a = warp_sum(a);
+            ac = warp_sum(ac);
+            if (lane == 0) {
+                const double ratio = a * P.inv_norm;
+                const double ratio_c = ac * P.inv_norm_c;
+                P.out[seg] = ratio;
+                P.err[seg] = fabs(ratio - ratio_c) / (3.0 * fabs(ratio));
+                if (!isfinite(ratio)) atomicOr(P.status, 1);
+                P.seg_count[seg] = 0u;   // ready for the next run
+            }
+        }
+        // the next iteration's first __syncthreads orders s_tile/s_last reuse
+    }
+}
+
+size_t coef_smem_bytes(int precision, int n_steps)
+{
+    return (size_t)n_steps * C_COUNT * (precision == NU_FP64 ? sizeof(double) : sizeof(float));
+}
+
+template <typename T, int TPT>
+static int launch_t(int block, int grid, size_t smem, const DevProblem* d_probs, const int* d_prefix,
+                    int n_probs, int n_tiles, unsigned* d_counter, cudaStream_t s)
+{
+    auto k = traj_kernel<T, TPT>;
+    if (smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return NU_ECUDA;
+    }
+    k<<<grid, block, smem, s>>>(d_probs, d_prefix, n_probs, n_tiles, d_counter);
+    if (cudaGetLastError() != cudaSuccess) return NU_ECUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+        count_launch();   // captured launches are counted when the graph is replayed
+    return NU_OK;
+}
+
+int launch_traj(int precision, int tpt, int block, int grid, size_t smem, const DevProblem* d_probs,
+                const int* d_prefix, int n_probs, int n_tiles, unsigned* d_counter, void* stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (precision == NU_FP64) {
+        if (tpt == 2) return launch_t<double, 2>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
+        return launch_t<double, 1>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
+    }
+    if (tpt == 2) return launch_t<float, 2>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
+    return launch_t<float, 1>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
+}
+
+template <typename T, int TPT>
+static int occ_t(int block, size_t smem, int* out)
+{
+    auto k = traj_kernel<T, TPT>;
+    if (smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return NU_ECUDA;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, block, smem) != cudaSuccess)
+        return NU_ECUDA;
+    return NU_OK;
+}
+
+int max_ctas_per_sm(int precision, int tpt, int block, size_t smem, int* out)
+{
+    if (precision == NU_FP64) return tpt == 2 ? occ_t<double, 2>(block, smem, out) : occ_t<double, 1>(block, smem, out);
+    return tpt == 2 ? occ_t<float, 2>(block, smem, out) : occ_t<float, 1>(block, smem, out);
+}
+
+}  // namespace nuprof
