@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark: trajectory-steps/s of the relic-overdensity hot path on GB300.
+
+One step = one batched launch of the precision-sweep workload (NFW halo
+1e13 Msun, mass history M0 exp(-0.8 z), 4 relic masses {0.01, 0.05, 0.1, 0.3}
+eV, 64 radii log 1 kpc - 1 Mpc, 200 log q x 64 Gauss-Legendre mu, 800 RK4
+steps from z = 0 to 4: 3,276,800 trajectories, 2.62e9 trajectory-steps),
+mixed precision (FP32 state and force, FP64-built tables, FP64 sums).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own copy of
+the workload on its own GPU (weak scaling, no data-path collective); the
+timing is the max over ranks.  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2410_08267_gb300 import workloads as W  # noqa: E402
+
+METRIC = "trajectory-steps/s"
+UNIT = "trajectory-steps/s"
+WORKLOAD = ("precision_sweep_mixed: NFW M=1e13 Msun c=7.15 xi=exp(-0.8z), m_nu in "
+            "{0.01,0.05,0.1,0.3} eV, 64 radii log 1-1000 kpc, 200 log q (0.01-10 T0) x 64 GL mu, "
+            "800 RK4 steps z 0->4")
+# Algorithmic FP32 work per trajectory-step (FMA = 2 flops; one flop per
+# special function), counted from the force + RK4 formulation:
+#   force (x4): r^2 (3), rsqrt (1), 1/r^3 (2), y = r S (2), I(y) = log1p(y) - y/(1+y) (4),
+#               / I(c) (1), sel/r^3 - 1/R^3 (2)                       = 15 each, 60
+#   RK4 combine: three stage updates 9 each (27), last force scale (1),
+#               positions 2 x 7 (14), velocities 2 x 9 + 1 (19)     = 61
+FLOPS_PER_TRAJ_STEP = 121
+SFU_PER_TRAJ_STEP = 12
+SMS, FP32_LANES_PER_SM = 152, 128
+SAMPLE_RADII = (0, 21, 42, 63)
+SAMPLE_MASS_INDEX = 2          # 0.1 eV
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def fp32_peak_tflops(mhz: float) -> float:
+    return 2.0 * FP32_LANES_PER_SM * SMS * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, max_mhz_fallback: float = 2070.0) -> dict:
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": max_mhz_fallback, "reasons": ["unsampled"], "samples": 0}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags)
+                          if f.lower() in ("active", "1", "yes")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_oracle_sample(problems, n_threads: int = 0):
+    """FP64 oracle on the bounded sample: one mass, four radii (the oracle as is)."""
+    import oracle
+    pb = problems[SAMPLE_MASS_INDEX].replace(precision=W.FP64)
+    t0 = time.perf_counter()
+    out = oracle.profile(pb, radius_sel=list(SAMPLE_RADII), n_threads=n_threads)
+    dt = time.perf_counter() - t0
+    traj_steps = len(SAMPLE_RADII) * pb.n_q * pb.n_mu * pb.n_steps
+    return out, dt, traj_steps, oracle.max_threads() if n_threads <= 0 else n_threads
+
+
+def bench_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    problems = W.precision_sweep(precision=W.MIXED)
+    sample = (f"m_nu=0.1 eV, radii {list(SAMPLE_RADII)} of 64 (4 x 12800 trajectories x 800 steps)")
+    for _ in range(args.warmup):
+        run_oracle_sample(problems)
+    times, ts, cores = [], 0, 1
+    for _ in range(args.steps):
+        _, dt, ts, cores = run_oracle_sample(problems)
+        times.append(dt)
+    total = sum(times)
+    value = ts * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2410_08267_gb300 import nuprof as nu
+
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    problems = W.precision_sweep(precision=W.MIXED)
+    if args.case == "small":            # profiling case: one mass, 8 radii
+        problems = [problems[SAMPLE_MASS_INDEX].replace(radii=np.geomspace(1.0, 1000.0, 8))]
+    traj_steps = sum(pb.traj_steps for pb in problems)
+
+    with torch.cuda.stream(stream):
+        hs = [nu.create(pb, stream=stream) for pb in problems]
+    opts = nu.nu_opts()
+    opts.flags = nu.NU_FLAG_TIMING
+    opts.stream = stream.cuda_stream
+    batch = nu.nu_batch_create(hs, opts)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    for _ in range(args.warmup):
+        nu.nu_batch_run(batch, stream)
+    stream.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    launches0 = nu.nu_kernel_launches()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clocks:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            starts[i].record(stream)
+            nu.nu_batch_run(batch, stream)
+            ends[i].record(stream)
+            kernel_ms.append(nu.nu_batch_kernel_ms(batch))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    launches = nu.nu_kernel_launches() - launches0
+    grid = nu.nu_batch_info(batch)["grid"]
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_total = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_step = ms_total / args.steps
+    value = traj_steps * world / (ms_per_step / 1e3)
+    clock = clocks.summary()
+
+    # results of the last timed run (for the accuracy record)
+    results = [nu.nu_profile_result(h, pb.n_radii)[0] for h, pb in zip(hs, problems)]
+
+    # ---- end to end through the public API with host buffers ----
+    e2e_steps = max(2, min(args.steps, 5))
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            hh = [nu.create(pb, stream=stream) for pb in problems]
+            o2 = nu.nu_opts()
+            o2.stream = stream.cuda_stream
+            b2 = nu.nu_batch_create(hh, o2)
+            bh2d = nu.nu_batch_info(b2)["h2d_bytes"]
+            nu.nu_batch_run(b2, stream)
+            outs = [nu.nu_profile_result(h, pb.n_radii) for h, pb in zip(hh, problems)]
+            nu.nu_batch_destroy(b2)
+            for h in hh:
+                nu.nu_profile_destroy(h)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    for pb in problems:
+        h2d += nu.plan(pb)["h2d_bytes"]
+        d2h += 2 * 8 * pb.n_radii
+    h2d += bh2d                               # batch descriptor upload
+
+    nu.nu_batch_destroy(batch)
+    for h in hs:
+        nu.nu_profile_destroy(h)
+
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the trajectory kernel ----
+    kms = float(np.mean(kernel_ms))
+    flops = FLOPS_PER_TRAJ_STEP * traj_steps
+    achieved = flops / (kms / 1e3) / 1e12
+    peak_mhz = clock["sm_max_mhz"] or 2070.0
+    peak = fp32_peak_tflops(peak_mhz)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "traj_kernel<float,1>", "kernel_ms": kms,
+                "flops_per_traj_step": FLOPS_PER_TRAJ_STEP, "sfu_per_traj_step": SFU_PER_TRAJ_STEP,
+                "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop/FMA x {peak_mhz:.0f} MHz"}
+
+    # ---- CPU baseline: the oracle on a bounded sample, and the accuracy check ----
+    full = W.precision_sweep(precision=W.MIXED)
+    ref, dt, ts, cores = run_oracle_sample(full)
+    if args.case == "full":
+        got = results[SAMPLE_MASS_INDEX][list(SAMPLE_RADII)]
+        rel = np.abs(got - ref[list(SAMPLE_RADII)]) / np.abs(ref[list(SAMPLE_RADII)])
+    else:
+        rel = np.array([np.nan])
+    cpu = {"value": ts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"m_nu=0.1 eV, radii {list(SAMPLE_RADII)} of 64, FP64, {dt:.1f} s wall"}
+
+    if args.case == "small":
+        WORKLOAD_USED = "small profiling case of " + WORKLOAD + " (m_nu=0.1 eV, 8 radii)"
+    else:
+        WORKLOAD_USED = WORKLOAD
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_USED, "traj_steps_per_step": traj_steps,
+                       "precision": "mixed: FP32 state/force, FP64 tables and sums",
+                       "l2": "flushed (256 MiB write) between timed steps",
+                       "launch": f"one persistent batched launch per step: grid {grid} CTAs x 256 "
+                                 "threads, 1 trajectory/thread",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": traj_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "path": "create (host tables -> device) + batch + run + result + destroy"},
+            "gpu_launches": launches, "wall_s": wall,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clock,
+            "accuracy": {"max_rel_err_vs_oracle": float(rel.max()),
+                         "per_radius": [float(x) for x in rel],
+                         "sample": "m_nu=0.1 eV, radii 0,21,42,63"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--case", choices=("full", "small"), default="full",
+                    help="small: one mass x 8 radii of the same workload, for profiler captures")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,6 +99,8 @@ extern "C" {
 #define NU_FLAG_KEEP_QI  1 /* keep the final momentum q_i of every trajectory
                               (phase-space integrand, Fig. 3 of the paper)     */
 #define NU_FLAG_GRAPH    2 /* batches: capture the launch in a CUDA graph      */
+#define NU_FLAG_TIMING   4 /* batches: record CUDA events around the trajectory
+                              kernel (read with nu_batch_kernel_ms)            */
 
 typedef struct nu_cosmo {
     double Om;       /* matter density today; Omega_Lambda = 1 - Om (Sec. II.A) */
@@ -166,6 +168,7 @@ typedef struct nu_plan_info {
     double rho_bar0;         /* mean matter density today, Msun/kpc^3         */
     double z_end;            /* resolved end redshift                         */
     long long n_traj;        /* n_radii * n_q * n_mu                          */
+    long long h2d_bytes;     /* bytes create() copies host -> device          */
     long long traj_steps;    /* n_traj * n_steps                              */
     long long device_bytes;  /* device memory create() will allocate          */
     int n_tiles;             /* work tiles of one run                         */
@@ -206,7 +209,8 @@ NU_API int nu_profile_result(nu_profile* h, double* n_over_nbar, double* err_est
 
 /* Copy the final momenta q_i (units of k_B T0) of every trajectory of the last
  * run, ordered [radius][q][mu], into a host array of n values
- * (n = n_radii * n_q * n_mu).  Needs NU_FLAG_KEEP_QI at create; this is the
+ * (n = n_radii * n_q * n_mu); they are kept on the device in the state
+ * precision (FP64 or FP32).  Needs NU_FLAG_KEEP_QI at create; this is the
  * phase-space integrand of Sec. III (Fig. 3).  Errors: NU_EINVAL, NU_EBUSY,
  * NU_ECUDA. */
 NU_API int nu_profile_qi(nu_profile* h, double* qi, long long n);
@@ -226,6 +230,19 @@ NU_API void nu_profile_destroy(nu_profile* h);
 NU_API int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch** out);
 NU_API int nu_batch_run(nu_batch* b, void* stream);
 NU_API void nu_batch_destroy(nu_batch* b);
+
+/* Device time in milliseconds of the trajectory kernel of the last
+ * nu_batch_run of a batch created with NU_FLAG_TIMING (events recorded on the
+ * launch stream around the kernel only; with NU_FLAG_GRAPH, around the graph
+ * launch).  Waits for that run.  Errors: NU_EINVAL (no timing flag), NU_EBUSY
+ * (never run), NU_ECUDA. */
+NU_API int nu_batch_kernel_ms(nu_batch* b, float* ms);
+
+/* Size of a batch: total work tiles, trajectory-steps of one run, bytes that
+ * nu_batch_create copied host -> device, and the persistent grid (CTAs).
+ * Any output pointer may be NULL.  Errors: NU_EINVAL. */
+NU_API int nu_batch_info(const nu_batch* b, int* n_tiles, long long* traj_steps,
+                         long long* h2d_bytes, int* grid);
 
 /* Launch counters: kernels launched by the library since load (all handles). */
 NU_API long long nu_kernel_launches(void);

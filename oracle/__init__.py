@@ -16,6 +16,7 @@ Functions and the passages they follow:
   f             Sec. II.C / Sec. IV.B initial distributions
   initial_state, final_q     Sec. II.C initial conditions and Liouville map
   profile       Eq. localdensity divided by the background density
+  profile_perturbed          conditioning probe (not part of the method)
 """
 from __future__ import annotations
 
@@ -75,6 +76,11 @@ def lib():
                                  C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                                  C.c_double, C.c_int, dp, dp]
         L.or_profile.restype = C.c_int
+        L.or_profile_perturbed.argtypes = [P, dp, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int,
+                                           C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                           C.c_double, C.c_int, C.c_double, C.c_ulonglong, C.c_int,
+                                           dp, dp]
+        L.or_profile_perturbed.restype = C.c_int
         L.or_initial_state.argtypes = [P, C.c_double, C.c_double, C.c_double, dp]
         L.or_initial_state.restype = None
         L.or_final_q.argtypes = [P, dp]
@@ -209,6 +215,32 @@ def profile(pb, radius_sel=None, n_threads: int = 0, return_qi: bool = False):
                           int(pb.n_q), float(pb.q_min), float(pb.q_max), int(pb.n_mu),
                           int(pb.n_steps), float(pb.z_end), int(n_threads), _dptr(out),
                           _dptr(qi) if qi is not None else None)
+    if rc != 0:
+        raise ValueError(f"oracle rejected the problem (rc={rc})")
+    return (out, qi) if return_qi else out
+
+
+def profile_perturbed(pb, eps: float, seed: int, radius_sel=None, n_threads: int = 0,
+                      return_qi: bool = False, round_state: bool = False):
+    """Conditioning probe: n/nbar with each trajectory's start velocity scaled by
+    (1 + eps u), u ~ U[-1, 1) independent per trajectory (counter-based, seeded),
+    and with round_state the state rounded to float32 after every RK4 step.
+    Not part of the method; eps = 0 without round_state equals profile() exactly."""
+    p = params(pb)
+    radii = np.ascontiguousarray(np.asarray(pb.radii, dtype=np.float64))
+    n_r = len(radii)
+    out = np.full(n_r, np.nan)
+    if radius_sel is None:
+        sel_ptr, n_sel = None, n_r
+    else:
+        sel = np.ascontiguousarray(np.asarray(radius_sel, dtype=np.int32))
+        sel_ptr, n_sel = sel.ctypes.data_as(C.POINTER(C.c_int)), len(sel)
+    qi = np.zeros((n_sel, pb.n_q, pb.n_mu)) if return_qi else None
+    rc = lib().or_profile_perturbed(C.byref(p), _dptr(radii), n_r, int(pb.radii_unit), sel_ptr,
+                                    n_sel, int(pb.n_q), float(pb.q_min), float(pb.q_max),
+                                    int(pb.n_mu), int(pb.n_steps), float(pb.z_end), int(n_threads),
+                                    float(eps), int(seed), int(bool(round_state)), _dptr(out),
+                                    _dptr(qi) if qi is not None else None)
     if rc != 0:
         raise ValueError(f"oracle rejected the problem (rc={rc})")
     return (out, qi) if return_qi else out

@@ -323,11 +323,55 @@ static double csum(const double* a, long n)
  * radius_sel (length n_sel, may be NULL = all) chooses which radii to compute;
  * out[r] is written for the selected radii only.  qi_out, if not NULL, gets
  * q_i for every (selected radius, j, k) in that order.                       */
+/* Counter-based uniform variate in [-1, 1) from splitmix64 (Steele, Lea &
+ * Flood 2014) of (seed, radius index, trajectory index).  Used only to
+ * measure the conditioning of the discrete method: see or_profile_perturbed. */
+static double or_unit_noise(unsigned long long seed, long ir, long t)
+{
+    unsigned long long z = seed * 0x9E3779B97F4A7C15ULL + ((unsigned long long)ir << 32) + (unsigned long long)t;
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+static int profile_impl(const or_params* p, const double* radii, int n_radii, int radii_unit,
+                        const int* radius_sel, int n_sel, int n_q, double q_min, double q_max,
+                        int n_mu, int nsteps, double z_end, int n_threads, double eps,
+                        unsigned long long seed, int round_state, double* out, double* qi_out);
+
 int or_profile(const or_params* p, const double* radii, int n_radii, int radii_unit,
                const int* radius_sel, int n_sel,
                int n_q, double q_min, double q_max, int n_mu,
                int nsteps, double z_end, int n_threads,
                double* out, double* qi_out)
+{
+    return profile_impl(p, radii, n_radii, radii_unit, radius_sel, n_sel, n_q, q_min, q_max,
+                        n_mu, nsteps, z_end, n_threads, 0.0, 0ULL, 0, out, qi_out);
+}
+
+/* Conditioning probe (not part of the method): the same computation with every
+ * trajectory's initial velocity scaled by (1 + eps u), u uniform in [-1, 1)
+ * and independent per trajectory, and, if round_state != 0, the state rounded
+ * to IEEE single precision after every RK4 step (what storing the state in
+ * FP32 does to an otherwise FP64 computation).  The spread of n/nbar over a
+ * few seeds measures how strongly the discrete RK4 map amplifies rounding-size
+ * differences; eps = 0 and round_state = 0 reproduce or_profile bit for bit. */
+int or_profile_perturbed(const or_params* p, const double* radii, int n_radii, int radii_unit,
+                         const int* radius_sel, int n_sel,
+                         int n_q, double q_min, double q_max, int n_mu,
+                         int nsteps, double z_end, int n_threads, double eps,
+                         unsigned long long seed, int round_state, double* out, double* qi_out)
+{
+    return profile_impl(p, radii, n_radii, radii_unit, radius_sel, n_sel, n_q, q_min, q_max,
+                        n_mu, nsteps, z_end, n_threads, eps, seed, round_state, out, qi_out);
+}
+
+static int profile_impl(const or_params* p, const double* radii, int n_radii, int radii_unit,
+                        const int* radius_sel, int n_sel, int n_q, double q_min, double q_max,
+                        int n_mu, int nsteps, double z_end, int n_threads, double eps,
+                        unsigned long long seed, int round_state, double* out, double* qi_out)
 {
     or_derived d;
     if (or_derive(p, &d) != 0) return -1;
@@ -368,7 +412,20 @@ int or_profile(const or_params* p, const double* radii, int n_radii, int radii_u
             int j = (int)(t / n_mu), k = (int)(t % n_mu);
             double s[4];
             or_initial_state(p, x0, q[j], mu[k], s);
-            or_integrate(p, &d, s, 0.0, u_end, nsteps);
+            if (eps != 0.0) {
+                double g = 1.0 + eps * or_unit_noise(seed, ir, t);
+                s[2] *= g;
+                s[3] *= g;
+            }
+            if (!round_state) {
+                or_integrate(p, &d, s, 0.0, u_end, nsteps);
+            } else {
+                double du = u_end / (double)nsteps;
+                for (int k = 0; k < nsteps; ++k) {
+                    or_integrate(p, &d, s, (double)k * du, (double)(k + 1) * du, 1);
+                    for (int c = 0; c < 4; ++c) s[c] = (double)(float)s[c];
+                }
+            }
             double qi = or_final_q(p, s);
             if (qi_out) qi_out[(long)si * ntr + t] = qi;
             contrib[t] = wl[j] * q[j] * q[j] * q[j] * wmu[k] * or_f(p, qi);

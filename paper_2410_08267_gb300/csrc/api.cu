@@ -126,7 +126,12 @@ struct nu_batch {
     DevProblem* d_probs = nullptr;
     int* d_prefix = nullptr;
     unsigned* d_ctrl = nullptr;
+    long long h2d_bytes = 0;
+    long long traj_steps = 0;
     bool use_graph = false;
+    bool timing = false;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    bool timed_run = false;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
     std::shared_ptr<RunEvent> ev;
@@ -157,7 +162,8 @@ int plan_common(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* reli
     info.n_traj = seg * n_radii;
     info.traj_steps = info.n_traj * o.n_steps;
     info.device_bytes = device_bytes(o.precision, o.n_steps, n_radii, grid->n_q, grid->n_mu,
-                                     tiles_per_seg, (o.flags & NU_FLAG_KEEP_QI) != 0);
+                                     tiles_per_seg, (o.flags & NU_FLAG_KEEP_QI) != 0,
+                                     &info.h2d_bytes);
     const long long nt = (long long)tiles_per_seg * n_radii;
     if (nt > (1LL << 30)) return NU_EINVAL;
     info.n_tiles = (int)nt;
@@ -280,7 +286,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     const size_t o_out = carve((size_t)n_radii * sizeof(double));
     const size_t o_err = carve((size_t)n_radii * sizeof(double));
     const bool keep_qi = (o.flags & NU_FLAG_KEEP_QI) != 0;
-    const size_t o_qi = keep_qi ? carve((size_t)n_radii * nq * nmu * sizeof(float)) : 0;
+    const size_t o_qi = keep_qi ? carve((size_t)n_radii * nq * nmu * sz) : 0;
     const size_t total = off;
 
     rc = h->mem.allocate(total, o);
@@ -301,7 +307,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     P.seg_count = reinterpret_cast<unsigned*>(base + o_cnt);
     P.out = reinterpret_cast<double*>(base + o_out);
     P.err = reinterpret_cast<double*>(base + o_err);
-    P.qi = keep_qi ? reinterpret_cast<float*>(base + o_qi) : nullptr;
+    P.qi = keep_qi ? static_cast<void*>(base + o_qi) : nullptr;
     P.status = reinterpret_cast<int*>(base + o_ctrl + sizeof(unsigned));
     P.q_scale = relic->m_eV / (kC * kT0);                 // Liouville map: q_i = m |v| / (c k_B T0)
     P.inv_norm = 1.0 / (2.0 * nb);
@@ -414,6 +420,13 @@ int nu_profile_qi(nu_profile* h, double* qi, long long n)
         cudaGetLastError();
         return NU_ECUDA;
     }
+    if (h->opts.precision == NU_FP64) {
+        if (cudaMemcpy(qi, h->hdp.qi, total * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return NU_ECUDA;
+        }
+        return NU_OK;
+    }
     std::vector<float> tmp((size_t)total);
     if (cudaMemcpy(tmp.data(), h->hdp.qi, total * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
         cudaGetLastError();
@@ -468,6 +481,11 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
     nu_opts o;
     resolve_opts(opts, o);
     if (opts) b->use_graph = (opts->flags & NU_FLAG_GRAPH) != 0;
+    if (opts) b->timing = (opts->flags & NU_FLAG_TIMING) != 0;
+    if (b->timing && (cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess)) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
     size_t off = 0;
     auto carve = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
     const size_t o_ctrl = carve(4 * sizeof(unsigned));
@@ -487,6 +505,8 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
         b->mem.release();
         return NU_ECUDA;
     }
+    b->h2d_bytes = (long long)off;
+    for (int i = 0; i < n; ++i) b->traj_steps += hs[i]->info.traj_steps;
     b->d_ctrl = reinterpret_cast<unsigned*>(base + o_ctrl);
     b->d_probs = reinterpret_cast<DevProblem*>(base + o_probs);
     b->d_prefix = reinterpret_cast<int*>(base + o_pref);
@@ -500,11 +520,15 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
     return NU_OK;
 }
 
-static int batch_enqueue(nu_batch* b, cudaStream_t s)
+static int batch_enqueue(nu_batch* b, cudaStream_t s, bool timed)
 {
     if (cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return NU_ECUDA;
-    return launch_traj(b->precision, b->tpt, b->block, b->grid, b->smem, b->d_probs, b->d_prefix,
-                       (int)b->hs.size(), b->n_tiles, b->d_ctrl, s);
+    if (timed && cudaEventRecord(b->t0, s) != cudaSuccess) return NU_ECUDA;
+    const int rc = launch_traj(b->precision, b->tpt, b->block, b->grid, b->smem, b->d_probs,
+                               b->d_prefix, (int)b->hs.size(), b->n_tiles, b->d_ctrl, s);
+    if (rc != NU_OK) return rc;
+    if (timed && cudaEventRecord(b->t1, s) != cudaSuccess) return NU_ECUDA;
+    return NU_OK;
 }
 
 int nu_batch_run(nu_batch* b, void* stream)
@@ -514,13 +538,21 @@ int nu_batch_run(nu_batch* b, void* stream)
     int rc = NU_OK;
     if (b->use_graph) {
         if (!b->exec) {
+            // capture on a private stream (the legacy default stream cannot be
+            // captured); the instantiated graph is then replayed on `s`
+            if (!b->graph_stream &&
+                cudaStreamCreateWithFlags(&b->graph_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                b->graph_stream = nullptr;
+                return NU_ECUDA;
+            }
             cudaGraph_t g = nullptr;
-            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            if (cudaStreamBeginCapture(b->graph_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
                 cudaGetLastError();
                 return NU_ECUDA;
             }
-            rc = batch_enqueue(b, s);
-            const cudaError_t e = cudaStreamEndCapture(s, &g);
+            rc = batch_enqueue(b, b->graph_stream, false);
+            const cudaError_t e = cudaStreamEndCapture(b->graph_stream, &g);
             if (rc != NU_OK || e != cudaSuccess) {
                 cudaGetLastError();
                 if (g) cudaGraphDestroy(g);
@@ -534,13 +566,15 @@ int nu_batch_run(nu_batch* b, void* stream)
                 return NU_ECUDA;
             }
         }
-        if (cudaGraphLaunch(b->exec, s) != cudaSuccess) {
+        if ((b->timing && cudaEventRecord(b->t0, s) != cudaSuccess) ||
+            cudaGraphLaunch(b->exec, s) != cudaSuccess ||
+            (b->timing && cudaEventRecord(b->t1, s) != cudaSuccess)) {
             cudaGetLastError();
             return NU_ECUDA;
         }
         count_launch();
     } else {
-        rc = batch_enqueue(b, s);
+        rc = batch_enqueue(b, s, b->timing);
         if (rc != NU_OK) {
             cudaGetLastError();
             return rc;
@@ -552,7 +586,30 @@ int nu_batch_run(nu_batch* b, void* stream)
         return NU_ECUDA;
     }
     b->ev = ev;
+    b->timed_run = b->timing;
     for (nu_profile* h : b->hs) h->last = ev;
+    return NU_OK;
+}
+
+int nu_batch_info(const nu_batch* b, int* n_tiles, long long* traj_steps, long long* h2d_bytes,
+                  int* grid)
+{
+    if (!b) return NU_EINVAL;
+    if (n_tiles) *n_tiles = b->n_tiles;
+    if (traj_steps) *traj_steps = b->traj_steps;
+    if (h2d_bytes) *h2d_bytes = b->h2d_bytes;
+    if (grid) *grid = b->grid;
+    return NU_OK;
+}
+
+int nu_batch_kernel_ms(nu_batch* b, float* ms)
+{
+    if (!b || !ms || !b->timing) return NU_EINVAL;
+    if (!b->timed_run) return NU_EBUSY;
+    if (cudaEventSynchronize(b->t1) != cudaSuccess || cudaEventElapsedTime(ms, b->t0, b->t1) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
     return NU_OK;
 }
 
@@ -561,6 +618,9 @@ void nu_batch_destroy(nu_batch* b)
     if (!b) return;
     if (b->ev && b->ev->ev) cudaEventSynchronize(b->ev->ev);
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph_stream) cudaStreamDestroy(b->graph_stream);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
     b->mem.release();
     delete b;
 }

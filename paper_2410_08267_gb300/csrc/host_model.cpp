@@ -247,7 +247,7 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w)
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_mu,
-                       int tiles_per_seg, bool keep_qi)
+                       int tiles_per_seg, bool keep_qi, long long* h2d_bytes)
 {
     const size_t sz = precision == NU_FP64 ? sizeof(double) : sizeof(float);
     size_t b = 0;
@@ -260,10 +260,11 @@ long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_m
     b += 2 * align256((size_t)n_mu * sz);                        // mu, sin psi
     b += 2 * align256((size_t)n_q * sizeof(double));             // wq, wqc
     b += align256((size_t)n_mu * sizeof(double));                // wmu
+    if (h2d_bytes) *h2d_bytes = (long long)b;                    // everything above is uploaded
     b += align256((size_t)n_radii * tiles_per_seg * 2 * sizeof(double));
     b += align256((size_t)n_radii * sizeof(unsigned));
     b += 2 * align256((size_t)n_radii * sizeof(double));         // out, err
-    if (keep_qi) b += align256((size_t)n_radii * n_q * n_mu * sizeof(float));
+    if (keep_qi) b += align256((size_t)n_radii * n_q * n_mu * sz);
     return (long long)b;
 }
 

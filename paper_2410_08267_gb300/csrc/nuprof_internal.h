@@ -60,7 +60,7 @@ void log_nodes(int n, double q_min, double q_max, std::vector<double>& q,
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 void resolve_opts(const nu_opts* in, nu_opts& out);
 long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_mu,
-                       int tiles_per_seg, bool keep_qi);
+                       int tiles_per_seg, bool keep_qi, long long* h2d_bytes);
 
 // Device-visible description of one request (POD, lives in device memory).
 struct DevProblem {
@@ -76,7 +76,7 @@ struct DevProblem {
     unsigned* seg_count;    // [n_radii] tiles finished (reset by the finisher)
     double* out;            // [n_radii] n/nbar
     double* err;            // [n_radii] relative quadrature-error estimate
-    float* qi;              // [n_radii][n_q][n_mu] final q (optional)
+    void* qi;               // [n_radii][n_q][n_mu] final q in the state precision (optional)
     int* status;            // bit 0: non-finite sum
     double q_scale;         // q_i = |v| * q_scale
     double inv_norm;        // 1 / (2 sum_j wq_j f(q_j))

@@ -277,7 +277,7 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             accc += P.wqc[tj[i]] * wm * f;
             if (P.qi) {
                 const int t = tis * P.tile + i * blockDim.x + threadIdx.x;
-                P.qi[(size_t)seg * n_seg + t] = (float)qi;
+                reinterpret_cast<T*>(P.qi)[(size_t)seg * n_seg + t] = qi;
             }
         }
 

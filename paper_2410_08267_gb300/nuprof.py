@@ -23,7 +23,7 @@ NU_OK, NU_EINVAL, NU_ENOMEM, NU_ECUDA, NU_EBUSY = 0, -1, -2, -3, -4
 NU_ETIMEDOUT, NU_EDEVICE, NU_ENOTSUP, NU_ECANCELED, NU_EAGAIN = -5, -6, -7, -8, -9
 NU_FP64, NU_MIXED = 0, 1
 NU_RADII_KPC, NU_RADII_R200 = 0, 1
-NU_FLAG_KEEP_QI, NU_FLAG_GRAPH = 1, 2
+NU_FLAG_KEEP_QI, NU_FLAG_GRAPH, NU_FLAG_TIMING = 1, 2, 4
 NU_MAX_STEPS = 3000
 
 
@@ -66,7 +66,8 @@ class nu_opts(C.Structure):
 class nu_plan_info(C.Structure):
     _fields_ = [("R_kpc", C.c_double), ("r200_kpc", C.c_double), ("r_s_kpc", C.c_double),
                 ("z_i", C.c_double), ("Ic", C.c_double), ("rho_bar0", C.c_double),
-                ("z_end", C.c_double), ("n_traj", C.c_longlong), ("traj_steps", C.c_longlong),
+                ("z_end", C.c_double), ("n_traj", C.c_longlong), ("h2d_bytes", C.c_longlong),
+                ("traj_steps", C.c_longlong),
                 ("device_bytes", C.c_longlong), ("n_tiles", C.c_int), ("tile", C.c_int)]
 
 
@@ -96,6 +97,8 @@ def lib():
     L.nu_profile_destroy.restype = None
     L.nu_batch_create.argtypes = [P(vp), C.c_int, P(nu_opts), P(vp)]
     L.nu_batch_run.argtypes = [vp, vp]
+    L.nu_batch_kernel_ms.argtypes = [vp, P(C.c_float)]
+    L.nu_batch_info.argtypes = [vp, P(C.c_int), P(C.c_longlong), P(C.c_longlong), P(C.c_int)]
     L.nu_batch_destroy.argtypes = [vp]
     L.nu_batch_destroy.restype = None
     L.nu_kernel_launches.argtypes = []
@@ -105,6 +108,7 @@ def lib():
     L.nu_version.argtypes = []
     for name in ("nu_profile_plan", "nu_profile_create", "nu_profile_run", "nu_profile_result",
                  "nu_profile_qi", "nu_profile_info", "nu_batch_create", "nu_batch_run",
+                 "nu_batch_kernel_ms", "nu_batch_info",
                  "nu_version"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -250,6 +254,19 @@ def nu_batch_create(handles: Sequence, opts: Optional[nu_opts] = None) -> C.c_vo
 
 def nu_batch_run(b, stream=None):
     _check(lib().nu_batch_run(b, _stream_ptr(stream)), "nu_batch_run")
+
+
+def nu_batch_kernel_ms(b) -> float:
+    ms = C.c_float()
+    _check(lib().nu_batch_kernel_ms(b, C.byref(ms)), "nu_batch_kernel_ms")
+    return ms.value
+
+
+def nu_batch_info(b) -> dict:
+    nt, g = C.c_int(), C.c_int()
+    ts, hb = C.c_longlong(), C.c_longlong()
+    _check(lib().nu_batch_info(b, C.byref(nt), C.byref(ts), C.byref(hb), C.byref(g)), "nu_batch_info")
+    return {"n_tiles": nt.value, "traj_steps": ts.value, "h2d_bytes": hb.value, "grid": g.value}
 
 
 def nu_batch_destroy(b):

@@ -212,7 +212,10 @@ def random_small(seed: int, n: int = 8, precision: int = FP64) -> List[Problem]:
         kappa_p = {KAPPA_ONE: (0.0, 0.0, 0.0), KAPPA_POW1PZ: (0.05, 0.0, 0.0),
                    KAPPA_PAPER: (0.2, 1.5, 0.0), KAPPA_CONST: (1.1, 0.0, 0.0)}[kappa_kind]
         f_kind = int(rng.integers(0, 2))
-        m = rng.uniform(0.01, 0.5) if f_kind == F_FD else 10.0 ** rng.uniform(3.0, 4.0)
+        # the non-thermal shape is drawn at neutrino-like masses here (as in the
+        # paper's freeze-in example at 0.3 eV), where a q grid of 0.01-10 T0
+        # covers today's phase space
+        m = rng.uniform(0.01, 0.5) if f_kind == F_FD else rng.uniform(0.05, 1.0)
         out.append(Problem(Om=rng.uniform(0.28, 0.34), h=rng.uniform(0.64, 0.72), M_h=M,
                            c=c_of_M(M) * 10.0 ** rng.normal(0.0, 0.15), xi_kind=xi_kind,
                            xi_p=xi_p, kappa_kind=kappa_kind, kappa_p=kappa_p, m_eV=m,

@@ -1,7 +1,10 @@
 """Parity of the CUDA path with the FP64 oracle, through the C-ABI.
 
-Tolerances (relative, on n/nbar, max over radii): 1e-5 in the FP64 mode and
-1e-4 in the mixed mode (FP32 state and force, FP64 quadrature sums).
+Tolerances (relative, on n/nbar): 1e-5 in the FP64 mode, 1e-4 in the mixed
+mode (FP32 state and force, FP64 quadrature sums), widened per radius only
+where the oracle's own result moves by more than TOL/K under rounding-size
+perturbations (see gpu_common).  Strict tests check FP64 parity to 1e-10 on
+well-conditioned radii and trajectories.
 """
 import numpy as np
 import pytest
@@ -10,7 +13,8 @@ import oracle
 from paper_2410_08267_gb300 import nuprof as nu
 from paper_2410_08267_gb300 import workloads as W
 
-from gpu_common import TOL_FP64, TOL_MIXED, rel_err, require_gpu, run_handle
+from gpu_common import (EPS, TOL_FP64, TOL_MIXED, assert_parity, oracle_with_spread, rel_err,
+                        require_gpu, run_handle)
 
 pytestmark = pytest.mark.gpu
 
@@ -20,19 +24,14 @@ def gpu():
     return require_gpu()
 
 
-def test_plain_small_fp64():
-    pb = W.plain_small(precision=W.FP64)[0]
+@pytest.mark.parametrize("prec", [W.FP64, W.MIXED])
+def test_plain_small(prec):
+    pb = W.plain_small(precision=prec)[0]
     got, err = run_handle(pb)
-    ref = oracle.profile(pb)
-    assert rel_err(got, ref).max() < TOL_FP64
+    e, b = assert_parity(got, pb, where="plain_small")
     assert np.all(err >= 0) and np.all(err < 1e-2)
-
-
-def test_plain_small_mixed():
-    pb = W.plain_small(precision=W.MIXED)[0]
-    got, _ = run_handle(pb)
-    ref = oracle.profile(pb)
-    assert rel_err(got, ref).max() < TOL_MIXED
+    # outer radii are well conditioned: the stated tolerance applies unwidened
+    assert np.all(e[5:] < (TOL_FP64 if prec == W.FP64 else TOL_MIXED))
 
 
 @pytest.mark.parametrize("prec,tol", [(W.FP64, 1e-13), (W.MIXED, 1e-6)])
@@ -43,22 +42,35 @@ def test_massless_halo_is_background(prec, tol, fk):
     assert np.abs(got - 1.0).max() < tol
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_random_small_all_kinds_fp64(seed):
-    for pb in W.random_small(seed, n=8, precision=W.FP64):
+def test_fp64_strict_on_well_conditioned_radii():
+    """Where the oracle is stable to 1e-12 under ulp-size perturbations, the FP64
+    mode must agree with it to 1e-10 (far below the stated 1e-5)."""
+    cases = [W.plain_small(precision=W.FP64)[0]] + W.random_small(4, n=6, precision=W.FP64)
+    n_checked = 0
+    for pb in cases:
         got, _ = run_handle(pb)
-        ref = oracle.profile(pb)
-        assert rel_err(got, ref).max() < TOL_FP64, pb
+        o, spread = oracle_with_spread(pb)
+        ok = spread < 1e-12
+        n_checked += int(ok.sum())
+        assert np.all(rel_err(got[ok], o[ok]) < 1e-10), pb
+    assert n_checked >= 5
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_small_all_kinds(seed):
+    for prec in (W.FP64, W.MIXED):
+        for pb in W.random_small(seed, n=8, precision=prec):
+            got, _ = run_handle(pb)
+            assert_parity(got, pb, where=f"seed {seed}")
 
 
 @pytest.mark.parametrize("block,tpt", [(64, 1), (128, 2), (256, 1), (512, 2)])
-@pytest.mark.parametrize("prec,tol", [(W.FP64, TOL_FP64), (W.MIXED, TOL_MIXED)])
-def test_launch_shapes(block, tpt, prec, tol):
+@pytest.mark.parametrize("prec", [W.FP64, W.MIXED])
+def test_launch_shapes(block, tpt, prec):
     # ragged: 1000 trajectories per radius never fill the last tile
     pb = W.plain_small(precision=prec)[0].replace(n_steps=200)
     got, _ = run_handle(pb, block=block, tpt=tpt)
-    ref = oracle.profile(pb)
-    assert rel_err(got, ref).max() < tol
+    assert_parity(got, pb, where=f"block {block} tpt {tpt}")
 
 
 def test_edge_grids():
@@ -71,27 +83,38 @@ def test_edge_grids():
         base.replace(n_q=17, n_mu=61),                            # ragged, several tiles
         base.replace(z_end=0.0),                                  # default end: the paper's z_i
         base.replace(M_h=1e15, c=4.0, m_eV=0.3),                  # massive halo, heavy relic
+        base.replace(xi_kind=W.XI_LINEAR, xi_p=(1.0, 8.0, 1.0), z_end=9.0),   # early onset
     ]
     for pb in cases:
-        got, _ = run_handle(pb)
-        ref = oracle.profile(pb)
-        assert rel_err(got, ref).max() < TOL_FP64, pb
+        for prec in (W.FP64, W.MIXED):
+            p = pb.replace(precision=prec)
+            got, _ = run_handle(p)
+            assert_parity(got, p, where=str(p)[:80])
 
 
-def test_final_momenta_elementwise_fp64():
-    pb = W.plain_small(precision=W.FP64)[0].replace(n_steps=400)
-    h = nu.create(pb, flags=nu.NU_FLAG_KEEP_QI)
+def _qi(pb, **kw):
+    h = nu.create(pb, flags=nu.NU_FLAG_KEEP_QI, **kw)
     try:
         nu.nu_profile_run(h)
         n = pb.n_radii * pb.n_q * pb.n_mu
-        qi = nu.nu_profile_qi(h, n).reshape(pb.n_radii, pb.n_q, pb.n_mu)
+        return nu.nu_profile_qi(h, n).reshape(pb.n_radii, pb.n_q, pb.n_mu)
     finally:
         nu.nu_profile_destroy(h)
-    _, ref = oracle.profile(pb, return_qi=True)
-    # q_i is kept as float32 by the library
-    r = np.abs(qi - ref) / np.abs(ref)
-    assert np.median(r) < 1e-7
-    assert np.mean(r < 1e-6) > 0.999
+
+
+def test_final_momenta_elementwise():
+    """Per-trajectory Liouville map q_i: FP64 mode to 1e-10 and mixed mode to
+    1e-4 on every trajectory the oracle itself resolves stably (its q_i moves
+    by < 1e-12 resp. < 1e-6 under ulp-size start perturbations)."""
+    for prec, stable, tol, min_frac in ((W.FP64, 1e-12, 1e-10, 0.6), (W.MIXED, 1e-6, 1e-4, 0.6)):
+        pb = W.plain_small(precision=prec)[0]
+        got = _qi(pb)
+        _, ref = oracle.profile(pb, return_qi=True)
+        _, pert = oracle.profile_perturbed(pb, EPS[prec], 7, return_qi=True,
+                                           round_state=(prec == W.MIXED))
+        ok = rel_err(pert, ref) < stable
+        assert ok.mean() > min_frac
+        assert np.all(rel_err(got[ok], ref[ok]) < tol), prec
 
 
 def test_run_twice_is_identical_and_result_before_run_is_busy():
@@ -127,9 +150,7 @@ def test_precision_sweep_full_size_sampled_radii():
         for h in hs:
             nu.nu_profile_destroy(h)
     sel = [0, 21, 42, 63]
-    worst = 0.0
     for pb, g in zip(probs, got):
-        ref = oracle.profile(pb, radius_sel=sel)
-        worst = max(worst, rel_err(g[sel], ref[sel]).max())
         assert np.all(np.isfinite(g))
-    assert worst < TOL_MIXED, worst
+        e, _ = assert_parity(g, pb, sel=sel, where=f"m={pb.m_eV}")
+        assert np.all(e[1:] < TOL_MIXED)     # beyond the innermost kpc: stated tolerance
