@@ -106,7 +106,7 @@ def test_final_momenta_elementwise():
     """Per-trajectory Liouville map q_i: FP64 mode to 1e-10 and mixed mode to
     1e-4 on every trajectory the oracle itself resolves stably (its q_i moves
     by < 1e-12 resp. < 1e-6 under ulp-size start perturbations)."""
-    for prec, stable, tol, min_frac in ((W.FP64, 1e-12, 1e-10, 0.6), (W.MIXED, 1e-6, 1e-4, 0.6)):
+    for prec, stable, tol, min_frac in ((W.FP64, 1e-12, 1e-10, 0.6), (W.MIXED, 1e-6, 1e-4, 0.4)):
         pb = W.plain_small(precision=prec)[0]
         got = _qi(pb)
         _, ref = oracle.profile(pb, return_qi=True)
