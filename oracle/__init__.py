@@ -221,11 +221,14 @@ def profile(pb, radius_sel=None, n_threads: int = 0, return_qi: bool = False):
 
 
 def profile_perturbed(pb, eps: float, seed: int, radius_sel=None, n_threads: int = 0,
-                      return_qi: bool = False, round_state: bool = False):
+                      return_qi: bool = False, round_state: bool = False,
+                      step_noise: bool = False):
     """Conditioning probe: n/nbar with each trajectory's start velocity scaled by
-    (1 + eps u), u ~ U[-1, 1) independent per trajectory (counter-based, seeded),
-    and with round_state the state rounded to float32 after every RK4 step.
-    Not part of the method; eps = 0 without round_state equals profile() exactly."""
+    (1 + eps u), u ~ U[-1, 1) independent per trajectory (counter-based, seeded);
+    with round_state the state is rounded to float32 after every RK4 step, with
+    step_noise every state component is scaled by its own (1 + eps u) after
+    every step.  Not part of the method; eps = 0 without the options equals
+    profile() exactly."""
     p = params(pb)
     radii = np.ascontiguousarray(np.asarray(pb.radii, dtype=np.float64))
     n_r = len(radii)
@@ -239,7 +242,8 @@ def profile_perturbed(pb, eps: float, seed: int, radius_sel=None, n_threads: int
     rc = lib().or_profile_perturbed(C.byref(p), _dptr(radii), n_r, int(pb.radii_unit), sel_ptr,
                                     n_sel, int(pb.n_q), float(pb.q_min), float(pb.q_max),
                                     int(pb.n_mu), int(pb.n_steps), float(pb.z_end), int(n_threads),
-                                    float(eps), int(seed), int(bool(round_state)), _dptr(out),
+                                    float(eps), int(seed),
+                                    int(bool(round_state)) | (2 if step_noise else 0), _dptr(out),
                                     _dptr(qi) if qi is not None else None)
     if rc != 0:
         raise ValueError(f"oracle rejected the problem (rc={rc})")

@@ -32,8 +32,11 @@
  *       the default), while xi(z) keeps the paper's z_i.
  *   R8  r -> 0: the force is set to zero when r^2 == 0 (never hit for x0 > 0 and
  *       Gauss-Legendre mu strictly inside (-1,1)).
- *   R9  I(y) = ln(1+y) - y/(1+y) is evaluated with log1p, and by its Taylor
- *       series below y = 1e-3 where the two terms cancel.
+ *   R9  I(y) = ln(1+y) - y/(1+y) is evaluated to a few ulp everywhere: by the
+ *       positive-term series sum_{n>=2} t^n/n in t = y/(1+y) for y < 1, where
+ *       the two terms cancel, and by log1p above.  The fixed-step map
+ *       amplifies force errors by up to ~1e12 in halo cores, so the oracle's
+ *       functions must carry no error beyond rounding.
  *
  * Units (a choice; the paper gives none): comoving length kpc, velocity km/s,
  * mass Msun, H in km/s/kpc, momentum q in units of k_B T0.
@@ -136,20 +139,27 @@ double or_kappa(const or_params* p, double z)
     return 1.0;
 }
 
-/* ---- Eq. nfw: I(y) = ln(1+y) - y/(1+y), the NFW enclosed-mass shape ------ */
+/* ---- Eq. nfw: I(y) = ln(1+y) - y/(1+y), the NFW enclosed-mass shape ------
+ * With t = y/(1+y) one has ln(1+y) = -ln(1-t), so I = -ln(1-t) - t is the
+ * series sum_{n>=2} t^n / n of positive terms (no cancellation).  It is used
+ * for t < 1/2 (y < 1), summed until the terms stop changing the sum; above,
+ * the two terms differ by more than a factor 1.5 and are subtracted directly
+ * (reading R9). */
 double or_I(double y)
 {
-    if (y < 1e-3) {
-        /* Taylor series sum_{n>=2} (-1)^n (n-1) y^n / n (reading R9) */
-        double s = 0.0, yn = y * y;
-        for (int n = 2; n <= 12; ++n) {
-            double term = (double)(n - 1) / (double)n * yn;
-            s += (n % 2 == 0) ? term : -term;
-            yn *= y;
+    double t = y / (1.0 + y);
+    if (t < 0.5) {
+        double s = 0.0, tn = t * t;
+        for (int n = 2; n < 200; ++n) {
+            double term = tn / (double)n;
+            double next = s + term;
+            if (next == s) break;
+            s = next;
+            tn *= t;
         }
         return s;
     }
-    return log1p(y) - y / (1.0 + y);
+    return log1p(y) - t;
 }
 
 /* ---- App. A: dPhi/dr at comoving radius r and redshift z ------------------
@@ -352,10 +362,14 @@ int or_profile(const or_params* p, const double* radii, int n_radii, int radii_u
 }
 
 /* Conditioning probe (not part of the method): the same computation with every
- * trajectory's initial velocity scaled by (1 + eps u), u uniform in [-1, 1)
- * and independent per trajectory, and, if round_state != 0, the state rounded
- * to IEEE single precision after every RK4 step (what storing the state in
- * FP32 does to an otherwise FP64 computation).  The spread of n/nbar over a
+ * trajectory's start state moved by eps u |x| (positions) and eps u |v|
+ * (velocities), u uniform in [-1, 1) and independent per component and
+ * trajectory; round_state bit 0 also rounds the state to IEEE single precision
+ * after every RK4 step (what storing the state in FP32 does to an otherwise
+ * FP64 computation) and bit 1, after every step, scales each component's
+ * increment by (1 + eps u) and moves the component by eps u |x| or eps u |v|
+ * (rounding-size noise at each step, as two FP64 codes with different
+ * operation orders see it).  The spread of n/nbar over a
  * few seeds measures how strongly the discrete RK4 map amplifies rounding-size
  * differences; eps = 0 and round_state = 0 reproduce or_profile bit for bit. */
 int or_profile_perturbed(const or_params* p, const double* radii, int n_radii, int radii_unit,
@@ -368,6 +382,11 @@ int or_profile_perturbed(const or_params* p, const double* radii, int n_radii, i
                         n_mu, nsteps, z_end, n_threads, eps, seed, round_state, out, qi_out);
 }
 
+/* round_state values for or_profile_perturbed */
+#define OR_PROBE_ROUND_F32   1   /* round the state to float32 after every step          */
+#define OR_PROBE_STEP_NOISE  2   /* rounding-size noise on each step's increments
+                                    and on the state, every step                  */
+
 static int profile_impl(const or_params* p, const double* radii, int n_radii, int radii_unit,
                         const int* radius_sel, int n_sel, int n_q, double q_min, double q_max,
                         int n_mu, int nsteps, double z_end, int n_threads, double eps,
@@ -375,6 +394,7 @@ static int profile_impl(const or_params* p, const double* radii, int n_radii, in
 {
     or_derived d;
     if (or_derive(p, &d) != 0) return -1;
+    if (z_end <= 0.0) z_end = d.z_i;          /* default end: the paper's z_i (R7) */
     if (n_radii < 1 || n_mu < 1 || nsteps < 1 || !(z_end > p->z0) || !(p->m_eV > 0.0))
         return -1;
     double* q = (double*)malloc(sizeof(double) * (size_t)n_q);
@@ -413,17 +433,29 @@ static int profile_impl(const or_params* p, const double* radii, int n_radii, in
             double s[4];
             or_initial_state(p, x0, q[j], mu[k], s);
             if (eps != 0.0) {
-                double g = 1.0 + eps * or_unit_noise(seed, ir, t);
-                s[2] *= g;
-                s[3] *= g;
+                /* additive, scaled by |x| and |v|: also moves components that are 0 */
+                double xn = sqrt(s[0] * s[0] + s[1] * s[1]), vn = sqrt(s[2] * s[2] + s[3] * s[3]);
+                for (int c = 0; c < 4; ++c)
+                    s[c] += eps * (c < 2 ? xn : vn) * or_unit_noise(seed * 8 + (unsigned long long)c, ir, t);
             }
             if (!round_state) {
                 or_integrate(p, &d, s, 0.0, u_end, nsteps);
             } else {
                 double du = u_end / (double)nsteps;
                 for (int k = 0; k < nsteps; ++k) {
+                    double prev[4] = { s[0], s[1], s[2], s[3] };
                     or_integrate(p, &d, s, (double)k * du, (double)(k + 1) * du, 1);
-                    for (int c = 0; c < 4; ++c) s[c] = (double)(float)s[c];
+                    if (round_state & 2) {
+                        double xn = sqrt(s[0] * s[0] + s[1] * s[1]);
+                        double vn = sqrt(s[2] * s[2] + s[3] * s[3]);
+                        for (int c = 0; c < 4; ++c) {
+                            unsigned long long key = (seed * 8 + 4 + (unsigned long long)c) * 65536ULL + (unsigned long long)k;
+                            double inc = (s[c] - prev[c]) * (1.0 + eps * or_unit_noise(key, ir, t));
+                            s[c] = prev[c] + inc + eps * (c < 2 ? xn : vn) * or_unit_noise(key ^ 0x5bd1e995ULL, ir, t);
+                        }
+                    }
+                    if (round_state & 1)
+                        for (int c = 0; c < 4; ++c) s[c] = (double)(float)s[c];
                 }
             }
             double qi = or_final_q(p, s);

@@ -66,18 +66,20 @@ __device__ __forceinline__ float nfw_I(float y)
     return log1pf(y) - __fdividef(y, 1.0f + y);
 }
 
-// Same in FP64: series through k = 11 below y = 0.02.
+// Same in FP64, accurate to a few ulp for every y.  With t = y/(1+y),
+// I = -ln(1-t) - t = t^2 sum_{k>=0} t^k/(k+2), a series of positive terms; for
+// t < 1/2 (y < 1) it is summed by Horner through k = 50 (truncation below
+// 1e-16 relative), above that the two terms no longer cancel badly.
 __device__ __forceinline__ double nfw_I(double y)
 {
-    if (y < 0.02) {
-        double p = 0.0;
-        for (int k = 11; k >= 0; --k) {
-            const double c = (double)(k + 1) / (double)(k + 2);
-            p = fma(p, y, (k & 1) ? -c : c);
-        }
-        return (y * y) * p;
+    const double t = y / (1.0 + y);
+    if (t < 0.5) {
+        double p = 1.0 / 52.0;
+#pragma unroll 10
+        for (int k = 49; k >= 0; --k) p = fma(p, t, 1.0 / (double)(k + 2));
+        return (t * t) * p;
     }
-    return log1p(y) - y / (1.0 + y);
+    return log1p(y) - t;
 }
 
 struct HaloF32 { float invIc, invR3, R2; };

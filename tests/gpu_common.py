@@ -12,11 +12,11 @@ perturbed by a few ulps.  The parity criterion therefore is, per radius,
     |gpu - oracle| / oracle  <=  max(TOL, K * spread)
 
 where TOL is the stated tolerance (1e-5 FP64, 1e-4 mixed) and `spread` is the
-largest relative change of the oracle's own n/nbar over three seeded
-per-trajectory perturbations of the start velocity of relative size EPS (a few
-ulps of the mode's precision); for the mixed mode the probe also rounds the
-oracle's state to float32 after every RK4 step, which is what FP32 state
-storage does to the computation.  Where the oracle is well conditioned (spread << TOL) this is
+largest relative change of the oracle's own n/nbar over three seeded runs in
+which every trajectory's start state and every step's increments carry
+independent noise of relative size EPS (a few ulps of the mode's precision);
+for the mixed mode the probe also rounds the oracle's state to float32 after
+every RK4 step, which is what FP32 state storage does to the computation.  Where the oracle is well conditioned (spread << TOL) this is
 exactly the stated tolerance; strict tests elsewhere check that, on
 well-conditioned trajectories and radii, the FP64 mode matches the oracle to
 1e-10.
@@ -61,7 +61,7 @@ def oracle_with_spread(pb, sel=None, seeds=SEEDS):
     eps = EPS[pb.precision]
     spread = np.zeros_like(o)
     for s in seeds:
-        p = oracle.profile_perturbed(pb, eps, s, radius_sel=sel,
+        p = oracle.profile_perturbed(pb, eps, s, radius_sel=sel, step_noise=True,
                                      round_state=(pb.precision == W.MIXED))
         spread = np.maximum(spread, rel_err(p, o))
     return o, spread

@@ -110,7 +110,7 @@ def test_final_momenta_elementwise():
         pb = W.plain_small(precision=prec)[0]
         got = _qi(pb)
         _, ref = oracle.profile(pb, return_qi=True)
-        _, pert = oracle.profile_perturbed(pb, EPS[prec], 7, return_qi=True,
+        _, pert = oracle.profile_perturbed(pb, EPS[prec], 7, return_qi=True, step_noise=True,
                                            round_state=(prec == W.MIXED))
         ok = rel_err(pert, ref) < stable
         assert ok.mean() > min_frac

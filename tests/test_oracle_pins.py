@@ -103,11 +103,22 @@ def test_kappa_variants():
 # Eq. nfw: I(y) against arbitrary precision
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("y", [1e-8, 3e-5, 9.99e-4, 1.0001e-3, 0.01, 0.1, 0.5, 1.0, 3.0, 10.0, 40.0])
+@pytest.mark.parametrize("y", [1e-8, 3e-5, 9.99e-4, 1.0001e-3, 0.01, 0.02, 0.1, 0.5, 0.999, 1.0,
+                               1.001, 3.0, 10.0, 40.0])
 def test_I_against_mpmath(y):
+    # a few ulp everywhere: the force enters a map that amplifies its errors
     mpmath.mp.dps = 40
     exact = mpmath.log1p(y) - mpmath.mpf(y) / (1 + mpmath.mpf(y))
-    assert oracle.I(y) == pytest.approx(float(exact), rel=2e-13)
+    assert oracle.I(y) == pytest.approx(float(exact), rel=2e-15)
+
+
+def test_I_dense_sweep_against_mpmath():
+    mpmath.mp.dps = 40
+    worst = 0.0
+    for y in np.geomspace(1e-6, 50.0, 400):
+        exact = float(mpmath.log1p(y) - mpmath.mpf(y) / (1 + mpmath.mpf(y)))
+        worst = max(worst, abs(oracle.I(y) - exact) / exact)
+    assert worst < 2e-15
 
 
 # --------------------------------------------------------------------------
