@@ -215,6 +215,16 @@ NU_API int nu_profile_result(nu_profile* h, double* n_over_nbar, double* err_est
  * NU_ECUDA. */
 NU_API int nu_profile_qi(nu_profile* h, double* qi, long long n);
 
+/* Verification of the force (App. A) exactly as the trajectory kernel computes
+ * it: for each of n comoving radii r[i] (kpc, on the x axis) writes
+ * m[i] = Mhat(r, z) / r^3 with Mhat = I(r/(r_s(1+z)))/I(c) - (r/R)^3 inside
+ * r200(1+z), 1 - (r/R)^3 inside R and 0 beyond, evaluated in the handle's
+ * precision at the redshift of RK stage `stage` (half-step index 0..2N:
+ * 1+z = exp(stage * ln(1+z_end) / (2N))).  The gradient is
+ * dPhi/dr = G kappa(z) (1+z) xi(z) M_h m r.  Host arrays; synchronous.
+ * Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
+NU_API int nu_profile_force(nu_profile* h, int stage, const double* r, int n, double* m);
+
 /* Plan numbers of an existing handle. */
 NU_API int nu_profile_info(const nu_profile* h, nu_plan_info* info);
 

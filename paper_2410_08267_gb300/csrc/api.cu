@@ -436,6 +436,27 @@ int nu_profile_qi(nu_profile* h, double* qi, long long n)
     return NU_OK;
 }
 
+int nu_profile_force(nu_profile* h, int stage, const double* r, int n, double* m)
+{
+    if (!h || !r || !m || n < 1 || stage < 0 || stage > 2 * h->opts.n_steps) return NU_EINVAL;
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, (size_t)n * 2 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ENOMEM;
+    }
+    double* d_r = static_cast<double*>(buf);
+    double* d_m = d_r + n;
+    int rc = NU_OK;
+    if (cudaMemcpy(d_r, r, (size_t)n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = NU_ECUDA;
+    if (rc == NU_OK) rc = launch_force_probe(h->opts.precision, h->d_prob, stage, d_r, n, d_m, nullptr);
+    if (rc == NU_OK && cudaMemcpy(m, d_m, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = NU_ECUDA;
+    if (rc != NU_OK) cudaGetLastError();
+    cudaFree(buf);
+    return rc;
+}
+
 int nu_profile_info(const nu_profile* h, nu_plan_info* info)
 {
     if (!h || !info) return NU_EINVAL;

@@ -95,6 +95,8 @@ int launch_traj(int precision, int tpt, int block, int grid, size_t smem_bytes,
                 unsigned* d_tile_counter, void* stream);
 int max_ctas_per_sm(int precision, int tpt, int block, size_t smem_bytes, int* out);
 size_t coef_smem_bytes(int precision, int n_steps);
+int launch_force_probe(int precision, const DevProblem* d_prob, int stage, const double* d_r, int n,
+                       double* d_out, void* stream);
 void count_launch();
 
 }  // namespace nuprof

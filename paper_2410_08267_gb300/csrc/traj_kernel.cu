@@ -46,24 +46,42 @@ __device__ __forceinline__ float rsqrt_approx(float v)
     return r;
 }
 
-// I(y) = ln(1+y) - y/(1+y) (Eq. nfw) in FP32.  Below y = 0.15 the two terms
-// cancel, so the Taylor series I/y^2 = sum_k (-1)^k (k+1)/(k+2) y^k is used
-// through k = 8 (truncation below 1e-7 relative there).
+__device__ __forceinline__ float lg2_approx(float v)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ float rcp_approx(float v)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// I(y) = ln(1+y) - y/(1+y) (Eq. nfw) in FP32.  For y < 1 the two terms cancel,
+// so I = y^2 P(y) with a degree-9 polynomial P fitted to I/y^2 on [0, 1]
+// (nfw_poly_fit.py; 3.5e-7 relative in float32 Horner).  Above, the terms
+// differ by more than a factor 1.5 and are subtracted directly, with the
+// hardware base-2 logarithm and reciprocal.
 __device__ __forceinline__ float nfw_I(float y)
 {
-    if (y < 0.15f) {
-        float p = 9.0f / 10.0f;
-        p = fmaf(p, y, -8.0f / 9.0f);
-        p = fmaf(p, y, 7.0f / 8.0f);
-        p = fmaf(p, y, -6.0f / 7.0f);
-        p = fmaf(p, y, 5.0f / 6.0f);
-        p = fmaf(p, y, -4.0f / 5.0f);
-        p = fmaf(p, y, 3.0f / 4.0f);
-        p = fmaf(p, y, -2.0f / 3.0f);
-        p = fmaf(p, y, 0.5f);
+    if (y < 1.0f) {
+        float p = -1.933632977e-02f;
+        p = fmaf(p, y, 1.171014905e-01f);
+        p = fmaf(p, y, -3.268344104e-01f);
+        p = fmaf(p, y, 5.741083622e-01f);
+        p = fmaf(p, y, -7.448884845e-01f);
+        p = fmaf(p, y, 8.059346676e-01f);
+        p = fmaf(p, y, -7.959684730e-01f);
+        p = fmaf(p, y, 7.496873736e-01f);
+        p = fmaf(p, y, -6.666569710e-01f);
+        p = fmaf(p, y, 4.999999404e-01f);
         return (y * y) * p;
     }
-    return log1pf(y) - __fdividef(y, 1.0f + y);
+    const float u = 1.0f + y;
+    return fmaf(lg2_approx(u), 0.693147180559945309f, -y * rcp_approx(u));
 }
 
 // Same in FP64, accurate to a few ulp for every y.  With t = y/(1+y),
@@ -85,26 +103,36 @@ __device__ __forceinline__ double nfw_I(double y)
 struct HaloF32 { float invIc, invR3, R2; };
 struct HaloF64 { double invIc, invR3, R2; };
 
+// The compensated halo's gradient vanishes beyond R, and the NFW term only
+// enters inside r200 (1+z): both tests are branches, so a warp whose lanes
+// are all beyond R (or all in the shell) skips that work.  The result is the
+// same value the full expression gives (0, resp. sel = 1).
 __device__ __forceinline__ float accel_m(float x, float y, float S, float Q, const HaloF32& hc)
 {
-    const float r2 = fmaxf(fmaf(x, x, y * y), 1e-20f);   // r -> 0 guard (below 1e-10 kpc)
-    const float rinv = rsqrt_approx(r2);
-    const float rinv3 = rinv * rinv * rinv;
-    const float ys = (r2 * rinv) * S;
-    const float sel = (r2 < Q) ? nfw_I(ys) * hc.invIc : 1.0f;
-    const float m = fmaf(sel, rinv3, -hc.invR3);
-    return (r2 < hc.R2) ? m : 0.0f;
+    const float r2 = fmaf(x, x, y * y);
+    float m = 0.0f;
+    if (r2 < hc.R2) {
+        const float rinv = rsqrt_approx(fmaxf(r2, 1e-20f));   // r -> 0 guard (below 1e-10 kpc)
+        const float rinv3 = rinv * rinv * rinv;
+        float sel = 1.0f;
+        if (r2 < Q) sel = nfw_I((r2 * rinv) * S) * hc.invIc;
+        m = fmaf(sel, rinv3, -hc.invR3);
+    }
+    return m;
 }
 
 __device__ __forceinline__ double accel_m(double x, double y, double S, double Q, const HaloF64& hc)
 {
-    const double r2 = fmax(fma(x, x, y * y), 1e-200);
-    const double rinv = rsqrt(r2);
-    const double rinv3 = rinv * rinv * rinv;
-    const double ys = (r2 * rinv) * S;
-    const double sel = (r2 < Q) ? nfw_I(ys) * hc.invIc : 1.0;
-    const double m = fma(sel, rinv3, -hc.invR3);
-    return (r2 < hc.R2) ? m : 0.0;
+    const double r2 = fma(x, x, y * y);
+    double m = 0.0;
+    if (r2 < hc.R2) {
+        const double rinv = rsqrt(fmax(r2, 1e-200));
+        const double rinv3 = rinv * rinv * rinv;
+        double sel = 1.0;
+        if (r2 < Q) sel = nfw_I((r2 * rinv) * S) * hc.invIc;
+        m = fma(sel, rinv3, -hc.invR3);
+    }
+    return m;
 }
 
 template <typename T> struct PrecTraits;
@@ -328,6 +356,39 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         }
         // the next iteration's first __syncthreads orders s_tile/s_last reuse
     }
+}
+
+// Force probe: m = Mhat/r^3 from the same device function the integrator
+// uses, at radius r[i] on the x axis and RK stage (half-step index) `stage`.
+template <typename T>
+__global__ void force_probe_kernel(const DevProblem* __restrict__ prob, int stage,
+                                   const double* __restrict__ r, int n, double* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const DevProblem& P = *prob;
+    const T* c = reinterpret_cast<const T*>(P.coef);
+    // stage 2k -> S0/Q0 of step k; 2k+1 -> S1/Q1 of step k; 2N -> S2/Q2 of step N-1
+    const int k = stage >= 2 * P.n_steps ? P.n_steps - 1 : stage / 2;
+    const int slot = stage >= 2 * P.n_steps ? 2 : (stage & 1);
+    const T S = c[(size_t)k * C_COUNT + C_S0 + slot];
+    const T Q = c[(size_t)k * C_COUNT + C_Q0 + slot];
+    const typename PrecTraits<T>::Halo hc = PrecTraits<T>::halo(P);
+    out[i] = (double)accel_m((T)r[i], T(0), S, Q, hc);
+}
+
+int launch_force_probe(int precision, const DevProblem* d_prob, int stage, const double* d_r, int n,
+                       double* d_out, void* stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int grid = (n + 127) / 128;
+    if (precision == NU_FP64)
+        force_probe_kernel<double><<<grid, 128, 0, s>>>(d_prob, stage, d_r, n, d_out);
+    else
+        force_probe_kernel<float><<<grid, 128, 0, s>>>(d_prob, stage, d_r, n, d_out);
+    if (cudaGetLastError() != cudaSuccess) return NU_ECUDA;
+    count_launch();
+    return NU_OK;
 }
 
 size_t coef_smem_bytes(int precision, int n_steps)

@@ -93,6 +93,7 @@ def lib():
     L.nu_profile_result.argtypes = [vp, P(C.c_double), P(C.c_double), C.c_int]
     L.nu_profile_qi.argtypes = [vp, P(C.c_double), C.c_longlong]
     L.nu_profile_info.argtypes = [vp, P(nu_plan_info)]
+    L.nu_profile_force.argtypes = [vp, C.c_int, P(C.c_double), C.c_int, P(C.c_double)]
     L.nu_profile_destroy.argtypes = [vp]
     L.nu_profile_destroy.restype = None
     L.nu_batch_create.argtypes = [P(vp), C.c_int, P(nu_opts), P(vp)]
@@ -107,7 +108,8 @@ def lib():
     L.nu_strerror.restype = C.c_char_p
     L.nu_version.argtypes = []
     for name in ("nu_profile_plan", "nu_profile_create", "nu_profile_run", "nu_profile_result",
-                 "nu_profile_qi", "nu_profile_info", "nu_batch_create", "nu_batch_run",
+                 "nu_profile_qi", "nu_profile_info", "nu_profile_force", "nu_batch_create",
+                 "nu_batch_run",
                  "nu_batch_kernel_ms", "nu_batch_info",
                  "nu_version"):
         getattr(L, name).restype = C.c_int
@@ -231,6 +233,13 @@ def nu_profile_qi(h, n: int) -> np.ndarray:
     qi = np.zeros(n)
     _check(lib().nu_profile_qi(h, _dptr(qi), int(n)), "nu_profile_qi")
     return qi
+
+
+def nu_profile_force(h, stage: int, r) -> np.ndarray:
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.float64))
+    m = np.zeros_like(r)
+    _check(lib().nu_profile_force(h, int(stage), _dptr(r), len(r), _dptr(m)), "nu_profile_force")
+    return m
 
 
 def nu_profile_info(h) -> dict:

@@ -223,6 +223,6 @@ def random_small(seed: int, n: int = 8, precision: int = FP64) -> List[Problem]:
                            radii=np.geomspace(1e-3, 2.0, int(rng.integers(1, 6))),
                            radii_unit=RADII_R200, n_q=int(rng.integers(2, 40)),
                            q_min=0.01, q_max=10.0, n_mu=int(rng.integers(1, 24)),
-                           n_steps=int(rng.integers(20, 120)), z_end=4.0,
+                           n_steps=int(rng.integers(60, 200)), z_end=4.0,
                            precision=precision))
     return out

