@@ -45,7 +45,8 @@ def test_massless_halo_is_background(prec, tol, fk):
 def test_fp64_strict_on_well_conditioned_radii():
     """Where the oracle is stable to 1e-12 under ulp-size perturbations, the FP64
     mode must agree with it to 1e-10 (far below the stated 1e-5)."""
-    cases = [W.plain_small(precision=W.FP64)[0]] + W.random_small(4, n=6, precision=W.FP64)
+    cases = ([W.plain_small(precision=W.FP64)[0]] + W.random_small(4, n=8, precision=W.FP64)
+             + W.random_small(5, n=8, precision=W.FP64))
     n_checked = 0
     for pb in cases:
         got, _ = run_handle(pb)
@@ -53,7 +54,7 @@ def test_fp64_strict_on_well_conditioned_radii():
         ok = spread < 1e-12
         n_checked += int(ok.sum())
         assert np.all(rel_err(got[ok], o[ok]) < 1e-10), pb
-    assert n_checked >= 5
+    assert n_checked >= 8
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
@@ -105,9 +106,9 @@ def _qi(pb, **kw):
 
 def test_final_momenta_elementwise():
     """Per-trajectory Liouville map q_i: FP64 mode to 1e-10 and mixed mode to
-    1e-4 on every trajectory the oracle itself resolves stably (its q_i moves
-    by < 1e-12 resp. < 1e-6 under ulp-size start perturbations)."""
-    for prec, stable, tol, min_frac in ((W.FP64, 1e-12, 1e-10, 0.6), (W.MIXED, 1e-6, 1e-4, 0.4)):
+    1e-4 on the trajectories the oracle itself resolves stably (its q_i moves
+    by < 1e-12 resp. < 1e-5 under rounding-size noise of the mode)."""
+    for prec, stable, tol, min_frac in ((W.FP64, 1e-12, 1e-10, 0.5), (W.MIXED, 1e-5, 1e-4, 0.3)):
         pb = W.plain_small(precision=prec)[0]
         got = _qi(pb)
         _, ref = oracle.profile(pb, return_qi=True)
