@@ -69,6 +69,8 @@ extern "C" {
 #define NU_ENOTSUP    -7   /* valid but unsupported combination                */
 #define NU_ECANCELED  -8   /* serving: the request was cancelled               */
 #define NU_EAGAIN     -9   /* serving: the request is not finished yet         */
+#define NU_ETOOBIG   -10   /* the request needs more than the static scratch
+                              of nu_profile_compute_noalloc                    */
 
 /* ---- halo growth xi(z) (Eq. rhototal; Sec. IV.A variants) ------------------ */
 #define NU_XI_STATIC  0    /* xi = 1 at every z: the NFW halo exists throughout */
@@ -253,6 +255,40 @@ NU_API int nu_batch_kernel_ms(nu_batch* b, float* ms);
  * Any output pointer may be NULL.  Errors: NU_EINVAL. */
 NU_API int nu_batch_info(const nu_batch* b, int* n_tiles, long long* traj_steps,
                          long long* h2d_bytes, int* grid);
+
+/* Maximum device scratch of nu_profile_compute_noalloc (a static array). */
+#define NU_NOALLOC_MAX_BYTES (4u << 20)
+
+/* One request computed without allocating anything, for callers that cannot
+ * call cudaMalloc (code whose device memory is owned by another framework's
+ * pool, hosts that forbid allocation after start-up, code running while
+ * another component captures work).  The paper has no counterpart: this is
+ * nu_profile_create + nu_profile_run + nu_profile_result in one synchronous
+ * call, with every device buffer the trajectory kernel needs (descriptor,
+ * coefficient table, nodes and weights, tile sums, counters) placed in one
+ * file-scope __device__ array of NU_NOALLOC_MAX_BYTES that every GPU loading
+ * the library keeps until the process exits, and the host tables built in a
+ * static host buffer.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *   Inputs are the same as nu_profile_create (opts may be NULL; opts->flags
+ *   must be 0 and the allocator hooks are ignored); n_over_nbar and err_est
+ *   (may be NULL) are host arrays of n_radii doubles.  The work runs on
+ *   `stream` and the call returns after it has finished.
+ *   Set-up: the first call on each device looks up the array's device
+ *   address (cudaGetSymbolAddress) with that device current; make that first
+ *   call before any stream capture.
+ *   Sharing: all calls use the same array.  A process-wide lock serializes
+ *   the calls and each waits for its own work, so calls from this library
+ *   never overlap; any other work that touched the array while a call ran
+ *   would race with it.  The array keeps the last call's contents; each call
+ *   clears the counters that must start at zero.
+ *   Errors: NU_EINVAL, NU_ENOTSUP, NU_ETOOBIG (the request needs more than
+ *   NU_NOALLOC_MAX_BYTES, e.g. too many radii x tiles or steps), NU_EDEVICE,
+ *   NU_ECUDA. */
+NU_API int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* halo,
+                                      const nu_relic* relic, const double* radii, int n_radii,
+                                      const nu_pgrid* p_grid, const nu_opts* opts,
+                                      double* n_over_nbar, double* err_est, void* stream);
 
 /* Launch counters: kernels launched by the library since load (all handles). */
 NU_API long long nu_kernel_launches(void);

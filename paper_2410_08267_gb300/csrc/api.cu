@@ -198,6 +198,7 @@ const char* nu_strerror(int code)
     case NU_ENOTSUP: return "unsupported combination";
     case NU_ECANCELED: return "cancelled";
     case NU_EAGAIN: return "not finished yet";
+    case NU_ETOOBIG: return "request exceeds the static scratch of the no-allocation entry point";
     default: return "unknown error";
     }
 }

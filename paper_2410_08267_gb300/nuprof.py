@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(HERE, "libnuprof.so")
 
 NU_OK, NU_EINVAL, NU_ENOMEM, NU_ECUDA, NU_EBUSY = 0, -1, -2, -3, -4
 NU_ETIMEDOUT, NU_EDEVICE, NU_ENOTSUP, NU_ECANCELED, NU_EAGAIN = -5, -6, -7, -8, -9
+NU_ETOOBIG = -10
+NU_NOALLOC_MAX_BYTES = 4 << 20
 NU_FP64, NU_MIXED = 0, 1
 NU_RADII_KPC, NU_RADII_R200 = 0, 1
 NU_FLAG_KEEP_QI, NU_FLAG_GRAPH, NU_FLAG_TIMING = 1, 2, 4
@@ -102,6 +104,10 @@ def lib():
     L.nu_batch_info.argtypes = [vp, P(C.c_int), P(C.c_longlong), P(C.c_longlong), P(C.c_int)]
     L.nu_batch_destroy.argtypes = [vp]
     L.nu_batch_destroy.restype = None
+    L.nu_profile_compute_noalloc.argtypes = [P(nu_cosmo), P(nu_halo), P(nu_relic), P(C.c_double),
+                                             C.c_int, P(nu_pgrid), P(nu_opts), P(C.c_double),
+                                             P(C.c_double), vp]
+    L.nu_profile_compute_noalloc.restype = C.c_int
     L.nu_kernel_launches.argtypes = []
     L.nu_kernel_launches.restype = C.c_longlong
     L.nu_strerror.argtypes = [C.c_int]
@@ -240,6 +246,20 @@ def nu_profile_force(h, stage: int, r) -> np.ndarray:
     m = np.zeros_like(r)
     _check(lib().nu_profile_force(h, int(stage), _dptr(r), len(r), _dptr(m)), "nu_profile_force")
     return m
+
+
+def nu_profile_compute_noalloc(cosmo, halo, relic, radii, grid, opts=None, stream=None):
+    """One request without any allocation (static device scratch); returns
+    (n/nbar, err_est) as host arrays."""
+    radii = np.ascontiguousarray(np.asarray(radii, dtype=np.float64))
+    out = np.zeros(len(radii))
+    err = np.zeros(len(radii))
+    _check(lib().nu_profile_compute_noalloc(C.byref(cosmo), C.byref(halo), C.byref(relic),
+                                            _dptr(radii), len(radii), C.byref(grid),
+                                            C.byref(opts) if opts is not None else None,
+                                            _dptr(out), _dptr(err), _stream_ptr(stream)),
+           "nu_profile_compute_noalloc")
+    return out, err
 
 
 def nu_profile_info(h) -> dict:
