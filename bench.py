@@ -38,14 +38,19 @@ UNIT = "trajectory-steps/s"
 WORKLOAD = ("precision_sweep_mixed: NFW M=1e13 Msun c=7.15 xi=exp(-0.8z), m_nu in "
             "{0.01,0.05,0.1,0.3} eV, 64 radii log 1-1000 kpc, 200 log q (0.01-10 T0) x 64 GL mu, "
             "800 RK4 steps z 0->4")
-# Algorithmic FP32 work per trajectory-step (FMA = 2 flops; one flop per
-# special function), counted from the force + RK4 formulation:
-#   force (x4): r^2 (3), rsqrt (1), 1/r^3 (2), y = r S (2), I(y) = log1p(y) - y/(1+y) (4),
-#               / I(c) (1), sel/r^3 - 1/R^3 (2)                       = 15 each, 60
-#   RK4 combine: three stage updates 9 each (27), last force scale (1),
-#               positions 2 x 7 (14), velocities 2 x 9 + 1 (19)     = 61
-FLOPS_PER_TRAJ_STEP = 121
-SFU_PER_TRAJ_STEP = 12
+# Algorithmic FP32 work (FMA = 2 flops, one flop per special function),
+# counted from the force + RK4 formulation.  The force has three branches
+# (App. A), so its work is data dependent and is counted exactly per run by
+# the library's branch tallies (nu_batch_branch_counts):
+#   force evaluation beyond R (gradient 0): r^2                          3
+#   in the compensating shell: + rsqrt 1, r^-3 2, sel/r^3 - 1/R^3 2      8
+#   in the NFW part: + y = r S 2, I(y) = log1p(y) - y/(1+y) 4, /I(c) 1   15
+#   RK4 combination per trajectory-step: three stage updates 9 each (27),
+#   last force scale (1), positions 2 x 7 (14), velocities 2 x 9 + 1 (19) 61
+# A full evaluation everywhere would be 4 x 15 + 61 = 121 per trajectory-step.
+FLOPS_EVAL = (3, 8, 15, 15)
+FLOPS_COMBINE = 61
+FLOPS_FULL = 121
 SMS, FP32_LANES_PER_SM = 152, 128
 SAMPLE_RADII = (0, 21, 42, 63)
 SAMPLE_MASS_INDEX = 2          # 0.1 eV
@@ -207,6 +212,7 @@ def bench_ours(args):
         wall = time.perf_counter() - wall0
     launches = nu.nu_kernel_launches() - launches0
     grid = nu.nu_batch_info(batch)["grid"]
+    counts = nu.nu_batch_branch_counts(batch, stream)     # untimed counting run
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_total = float(sum(step_ms))
     if dist is not None:
@@ -256,14 +262,17 @@ def bench_ours(args):
 
     # ---- roofline of the trajectory kernel ----
     kms = float(np.mean(kernel_ms))
-    flops = FLOPS_PER_TRAJ_STEP * traj_steps
+    flops = FLOPS_COMBINE * traj_steps + sum(f * c for f, c in zip(FLOPS_EVAL, counts))
     achieved = flops / (kms / 1e3) / 1e12
     peak_mhz = clock["sm_max_mhz"] or 2070.0
     peak = fp32_peak_tflops(peak_mhz)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "traj_kernel<float,1>", "kernel_ms": kms,
-                "flops_per_traj_step": FLOPS_PER_TRAJ_STEP, "sfu_per_traj_step": SFU_PER_TRAJ_STEP,
+                "flops_per_launch": flops, "flops_per_traj_step": flops / traj_steps,
+                "branch_counts": {"beyond_R": counts[0], "shell": counts[1],
+                                  "nfw_poly": counts[2], "nfw_log": counts[3]},
+                "full_eval_equiv_tflops": FLOPS_FULL * traj_steps / (kms / 1e3) / 1e12,
                 "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop/FMA x {peak_mhz:.0f} MHz"}
 
     # ---- CPU baseline: the oracle on a bounded sample, and the accuracy check ----

@@ -175,6 +175,8 @@ typedef struct nu_plan_info {
     long long device_bytes;  /* device memory create() will allocate          */
     int n_tiles;             /* work tiles of one run                         */
     int tile;                /* trajectories per tile (block * tpt)           */
+    int precision;           /* NU_FP64 or NU_MIXED                           */
+    int n_steps;             /* RK4 steps                                     */
 } nu_plan_info;
 
 /* Fill *info for the request (validation + Sec. II.B derivation + sizing).
@@ -238,7 +240,9 @@ NU_API void nu_profile_destroy(nu_profile* h);
  * precision and tile shape; each keeps its own outputs, read with
  * nu_profile_result.  The handles must outlive the batch.  opts may be NULL;
  * opts->flags & NU_FLAG_GRAPH captures the launch in a CUDA graph at the
- * first run and replays it afterwards.  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
+ * first run and replays it afterwards; opts->block and opts->tpt (when non-zero)
+ * set the batch's tile shape, else the requests' own shape is used (and must
+ * agree).  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
 NU_API int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch** out);
 NU_API int nu_batch_run(nu_batch* b, void* stream);
 NU_API void nu_batch_destroy(nu_batch* b);
@@ -249,6 +253,39 @@ NU_API void nu_batch_destroy(nu_batch* b);
  * launch).  Waits for that run.  Errors: NU_EINVAL (no timing flag), NU_EBUSY
  * (never run), NU_ECUDA. */
 NU_API int nu_batch_kernel_ms(nu_batch* b, float* ms);
+
+/* Exact branch statistics of one run of the batch, from a counting variant of
+ * the trajectory kernel (launched once, synchronously, on `stream`; it does not
+ * write the requests' results): counts[0] force evaluations beyond R (gradient
+ * exactly zero), counts[1] in the compensating shell, counts[2] in the NFW part
+ * with I(y) on its polynomial branch (y < 1), counts[3] on its logarithm
+ * branch.  Every trajectory slot that was integrated is counted: with one
+ * trajectory per thread that is exactly the requests' trajectories, with two
+ * a padding slot of a ragged tile runs beside a real one.  The force is data dependent (App. A has three branches), so these
+ * counts turn the work of a run into an exact algorithmic flop count.
+ * Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
+NU_API int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts);
+
+/* Launch-shape autotuner: times the batch of requests `hs` with each candidate
+ * tile shape (threads per CTA x trajectories per thread: 128x1, 256x1, 512x1,
+ * 64x2, 128x2, 256x2; one warm-up and the median of three runs) and reports the
+ * fastest.  With cache_path != NULL, a JSON-lines cache keyed by GPU name,
+ * precision, step-count and trajectory-count buckets (powers of two) is read
+ * first and appended to after tuning.  Results of different shapes agree to
+ * rounding, not bit for bit (the reduction order changes).  All requests must
+ * share a precision.  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
+typedef struct nu_tune_result {
+    int block;               /* best threads per CTA                          */
+    int tpt;                 /* best trajectories per thread                  */
+    float best_ms;           /* trajectory-kernel time of one run with it     */
+    int from_cache;          /* 1 if read from the cache (no timing done)     */
+    int n_candidates;
+    int cand_block[8];
+    int cand_tpt[8];
+    float cand_ms[8];
+} nu_tune_result;
+NU_API int nu_autotune(nu_profile* const* hs, int n, void* stream, const char* cache_path,
+                       nu_tune_result* out);
 
 /* Size of a batch: total work tiles, trajectory-steps of one run, bytes that
  * nu_batch_create copied host -> device, and the persistent grid (CTAs).

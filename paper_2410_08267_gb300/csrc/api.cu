@@ -128,6 +128,7 @@ struct nu_batch {
     unsigned* d_ctrl = nullptr;
     long long h2d_bytes = 0;
     long long traj_steps = 0;
+    unsigned long long* d_tallies = nullptr;   // [4], allocated at the first count
     bool use_graph = false;
     bool timing = false;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -161,13 +162,16 @@ int plan_common(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* reli
     info.z_end = d.z_end;
     info.n_traj = seg * n_radii;
     info.traj_steps = info.n_traj * o.n_steps;
+    const int tps_alloc = (int)((seg + kMinTile - 1) / kMinTile);
     info.device_bytes = device_bytes(o.precision, o.n_steps, n_radii, grid->n_q, grid->n_mu,
-                                     tiles_per_seg, (o.flags & NU_FLAG_KEEP_QI) != 0,
+                                     tps_alloc, (o.flags & NU_FLAG_KEEP_QI) != 0,
                                      &info.h2d_bytes);
     const long long nt = (long long)tiles_per_seg * n_radii;
     if (nt > (1LL << 30)) return NU_EINVAL;
     info.n_tiles = (int)nt;
     info.tile = tile;
+    info.precision = o.precision;
+    info.n_steps = o.n_steps;
     return NU_OK;
 }
 
@@ -282,7 +286,9 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     const size_t o_wqc = carve((size_t)nq * sizeof(double));
     const size_t o_wmu = carve((size_t)nmu * sizeof(double));
     const size_t upload_end = off;                         // everything above is uploaded
-    const size_t o_part = carve((size_t)n_radii * tps * 2 * sizeof(double));
+    // tile sums sized for the smallest tile shape, so that any batch shape fits
+    const size_t tps_alloc = (size_t)(((long long)nq * nmu + kMinTile - 1) / kMinTile);
+    const size_t o_part = carve((size_t)n_radii * tps_alloc * 2 * sizeof(double));
     const size_t o_cnt = carve((size_t)n_radii * sizeof(unsigned));
     const size_t o_out = carve((size_t)n_radii * sizeof(double));
     const size_t o_err = carve((size_t)n_radii * sizeof(double));
@@ -479,22 +485,36 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
     if (!hs || n < 1 || !out) return NU_EINVAL;
     std::unique_ptr<nu_batch> b(new (std::nothrow) nu_batch());
     if (!b) return NU_ENOMEM;
+    // tile shape: opts->block / opts->tpt when given, else the requests' own
+    // (which must then agree); precision must always agree
+    const int want_block = opts ? opts->block : 0;
+    const int want_tpt = opts ? opts->tpt : 0;
+    if ((want_block != 0 && (want_block < 64 || want_block > 512 || want_block % 32 != 0)) ||
+        (want_tpt != 0 && want_tpt != 1 && want_tpt != 2))
+        return NU_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!hs[i]) return NU_EINVAL;
         const nu_opts& o = hs[i]->opts;
         if (i == 0) {
             b->precision = o.precision;
-            b->tpt = o.tpt;
-            b->block = o.block;
-        } else if (o.precision != b->precision || o.tpt != b->tpt || o.block != b->block) {
+            b->tpt = want_tpt ? want_tpt : o.tpt;
+            b->block = want_block ? want_block : o.block;
+        } else if (o.precision != b->precision || (!want_tpt && o.tpt != b->tpt) ||
+                   (!want_block && o.block != b->block)) {
             return NU_EINVAL;
         }
         b->smem = std::max(b->smem, hs[i]->smem);
         b->hs.push_back(hs[i]);
     }
+    const int tile = b->block * b->tpt;
+    std::vector<DevProblem> descs(n);
     std::vector<int> prefix(n + 1, 0);
     for (int i = 0; i < n; ++i) {
-        const long long next = (long long)prefix[i] + hs[i]->n_tiles;
+        descs[i] = hs[i]->hdp;
+        const long long seg = (long long)hs[i]->grid.n_q * hs[i]->grid.n_mu;
+        descs[i].tile = tile;
+        descs[i].tiles_per_seg = (int)((seg + tile - 1) / tile);
+        const long long next = (long long)prefix[i] + (long long)descs[i].tiles_per_seg * hs[i]->n_radii;
         if (next > (1LL << 30)) return NU_EINVAL;
         prefix[i + 1] = (int)next;
     }
@@ -517,7 +537,7 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
     if (rc != NU_OK) return rc;
     std::vector<unsigned char> stage(off, 0);
     for (int i = 0; i < n; ++i)
-        std::memcpy(stage.data() + o_probs + i * sizeof(DevProblem), &hs[i]->hdp, sizeof(DevProblem));
+        std::memcpy(stage.data() + o_probs + i * sizeof(DevProblem), &descs[i], sizeof(DevProblem));
     std::memcpy(stage.data() + o_pref, prefix.data(), (n + 1) * sizeof(int));
     unsigned char* base = static_cast<unsigned char*>(b->mem.ptr);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
@@ -613,6 +633,35 @@ int nu_batch_run(nu_batch* b, void* stream)
     return NU_OK;
 }
 
+int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts)
+{
+    if (!b || !counts) return NU_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!b->d_tallies && cudaMalloc(&b->d_tallies, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        b->d_tallies = nullptr;
+        return NU_ENOMEM;
+    }
+    unsigned long long host[4] = {0, 0, 0, 0};
+    int rc = NU_OK;
+    if (cudaMemsetAsync(b->d_tallies, 0, sizeof(host), s) != cudaSuccess ||
+        cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess)
+        rc = NU_ECUDA;
+    if (rc == NU_OK)
+        rc = launch_traj_tally(b->precision, b->tpt, b->block, b->grid, b->smem, b->d_probs,
+                               b->d_prefix, (int)b->hs.size(), b->n_tiles, b->d_ctrl, b->d_tallies, s);
+    if (rc == NU_OK && (cudaMemcpyAsync(host, b->d_tallies, sizeof(host), cudaMemcpyDeviceToHost, s) !=
+                            cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+        rc = NU_ECUDA;
+    if (rc != NU_OK) {
+        cudaGetLastError();
+        return rc;
+    }
+    for (int k = 0; k < 4; ++k) counts[k] = (long long)host[k];
+    return NU_OK;
+}
+
 int nu_batch_info(const nu_batch* b, int* n_tiles, long long* traj_steps, long long* h2d_bytes,
                   int* grid)
 {
@@ -643,6 +692,7 @@ void nu_batch_destroy(nu_batch* b)
     if (b->graph_stream) cudaStreamDestroy(b->graph_stream);
     if (b->t0) cudaEventDestroy(b->t0);
     if (b->t1) cudaEventDestroy(b->t1);
+    if (b->d_tallies) cudaFree(b->d_tallies);
     b->mem.release();
     delete b;
 }

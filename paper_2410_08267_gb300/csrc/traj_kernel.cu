@@ -21,6 +21,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <type_traits>
 
 #include "nuprof_internal.h"
 
@@ -103,11 +104,25 @@ __device__ __forceinline__ double nfw_I(double y)
 struct HaloF32 { float invIc, invR3, R2; };
 struct HaloF64 { double invIc, invR3, R2; };
 
+// Branch tallies of force evaluations, kept only by the counting variant of the
+// kernel (used once, untimed, to turn the data-dependent work into an exact
+// algorithmic flop count): beyond R, shell, NFW part on the polynomial branch
+// of I(y), NFW part on the logarithm branch.
+struct NoTally {
+    __device__ __forceinline__ void add(int) {}
+};
+struct Tally {
+    unsigned n[4] = {0u, 0u, 0u, 0u};
+    __device__ __forceinline__ void add(int k) { ++n[k]; }
+};
+
 // The compensated halo's gradient vanishes beyond R, and the NFW term only
 // enters inside r200 (1+z): both tests are branches, so a warp whose lanes
 // are all beyond R (or all in the shell) skips that work.  The result is the
 // same value the full expression gives (0, resp. sel = 1).
-__device__ __forceinline__ float accel_m(float x, float y, float S, float Q, const HaloF32& hc)
+template <class Ctr = NoTally>
+__device__ __forceinline__ float accel_m(float x, float y, float S, float Q, const HaloF32& hc,
+                                         Ctr& ctr)
 {
     const float r2 = fmaf(x, x, y * y);
     float m = 0.0f;
@@ -115,13 +130,23 @@ __device__ __forceinline__ float accel_m(float x, float y, float S, float Q, con
         const float rinv = rsqrt_approx(fmaxf(r2, 1e-20f));   // r -> 0 guard (below 1e-10 kpc)
         const float rinv3 = rinv * rinv * rinv;
         float sel = 1.0f;
-        if (r2 < Q) sel = nfw_I((r2 * rinv) * S) * hc.invIc;
+        if (r2 < Q) {
+            const float ys = (r2 * rinv) * S;
+            ctr.add(ys < 1.0f ? 2 : 3);
+            sel = nfw_I(ys) * hc.invIc;
+        } else {
+            ctr.add(1);
+        }
         m = fmaf(sel, rinv3, -hc.invR3);
+    } else {
+        ctr.add(0);
     }
     return m;
 }
 
-__device__ __forceinline__ double accel_m(double x, double y, double S, double Q, const HaloF64& hc)
+template <class Ctr = NoTally>
+__device__ __forceinline__ double accel_m(double x, double y, double S, double Q,
+                                          const HaloF64& hc, Ctr& ctr)
 {
     const double r2 = fma(x, x, y * y);
     double m = 0.0;
@@ -129,8 +154,16 @@ __device__ __forceinline__ double accel_m(double x, double y, double S, double Q
         const double rinv = rsqrt(fmax(r2, 1e-200));
         const double rinv3 = rinv * rinv * rinv;
         double sel = 1.0;
-        if (r2 < Q) sel = nfw_I((r2 * rinv) * S) * hc.invIc;
+        if (r2 < Q) {
+            const double ys = (r2 * rinv) * S;
+            ctr.add(ys < 1.0 ? 2 : 3);
+            sel = nfw_I(ys) * hc.invIc;
+        } else {
+            ctr.add(1);
+        }
         m = fma(sel, rinv3, -hc.invR3);
+    } else {
+        ctr.add(0);
     }
     return m;
 }
@@ -178,26 +211,26 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // One classical RK4 step of size -h for one trajectory (Eq. eoms in ln a).
 // c points at the step's 16 coefficients (see CoefSlot).
-template <typename T>
+template <typename T, class Ctr>
 __device__ __forceinline__ void rk4_step(T& x, T& y, T& vx, T& vy, const T* c,
-                                         const typename PrecTraits<T>::Halo& hc)
+                                         const typename PrecTraits<T>::Halo& hc, Ctr& ctr)
 {
-    const T m1 = accel_m(x, y, c[C_S0], c[C_Q0], hc);
+    const T m1 = accel_m(x, y, c[C_S0], c[C_Q0], hc, ctr);
     const T p1 = c[C_B1] * m1;
     const T X2 = x + c[C_MA1] * vx, Y2 = y + c[C_MA1] * vy;
     const T VX2 = vx + p1 * x, VY2 = vy + p1 * y;
 
-    const T m2 = accel_m(X2, Y2, c[C_S1], c[C_Q1], hc);
+    const T m2 = accel_m(X2, Y2, c[C_S1], c[C_Q1], hc, ctr);
     const T p2 = c[C_B2] * m2;
     const T X3 = x + c[C_MA2] * VX2, Y3 = y + c[C_MA2] * VY2;
     const T VX3 = vx + p2 * X2, VY3 = vy + p2 * Y2;
 
-    const T m3 = accel_m(X3, Y3, c[C_S1], c[C_Q1], hc);
+    const T m3 = accel_m(X3, Y3, c[C_S1], c[C_Q1], hc, ctr);
     const T p3 = c[C_B3] * m3;
     const T X4 = x + c[C_MA3] * VX3, Y4 = y + c[C_MA3] * VY3;
     const T VX4 = vx + p3 * X3, VY4 = vy + p3 * Y3;
 
-    const T m4 = accel_m(X4, Y4, c[C_S2], c[C_Q2], hc);
+    const T m4 = accel_m(X4, Y4, c[C_S2], c[C_Q2], hc, ctr);
     const T p4 = c[C_B4] * m4;
 
     // x' = x - (h/6) (A_a v + 2 A_m V2 + 2 A_m V3 + A_b V4)
@@ -214,11 +247,14 @@ __device__ __forceinline__ void rk4_step(T& x, T& y, T& vx, T& vy, const T* c,
     vy = nvy;
 }
 
-template <typename T, int TPT>
+template <typename T, int TPT, bool COUNT>
 __global__ void __launch_bounds__(512)
 traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_prefix,
-            int n_probs, int n_tiles, unsigned* __restrict__ tile_counter)
+            int n_probs, int n_tiles, unsigned* __restrict__ tile_counter,
+            unsigned long long* __restrict__ tallies)
 {
+    using Ctr = typename std::conditional<COUNT, Tally, NoTally>::type;
+    Ctr ctr;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s_coef = reinterpret_cast<T*>(smem_raw);
     __shared__ int s_tile;
@@ -290,7 +326,7 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                 for (int q = 0; q < (int)(C_COUNT * sizeof(T) / 16); ++q)
                     reinterpret_cast<float4*>(c)[q] = c4[q];
 #pragma unroll
-                for (int i = 0; i < TPT; ++i) rk4_step<T>(x[i], y[i], vx[i], vy[i], c, hc);
+                for (int i = 0; i < TPT; ++i) rk4_step<T, Ctr>(x[i], y[i], vx[i], vy[i], c, hc, ctr);
             }
         }
 
@@ -356,6 +392,18 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         }
         // the next iteration's first __syncthreads orders s_tile/s_last reuse
     }
+    if constexpr (COUNT) {
+        // inactive padding lanes integrate a copy of trajectory 0; the tallies
+        // count every lane that ran, so the host subtracts nothing: the padding
+        // work is real work the kernel did
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            unsigned long long v = ctr.n[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) atomicAdd(&tallies[k], v);
+        }
+    }
 }
 
 // Force probe: m = Mhat/r^3 from the same device function the integrator
@@ -374,7 +422,8 @@ __global__ void force_probe_kernel(const DevProblem* __restrict__ prob, int stag
     const T S = c[(size_t)k * C_COUNT + C_S0 + slot];
     const T Q = c[(size_t)k * C_COUNT + C_Q0 + slot];
     const typename PrecTraits<T>::Halo hc = PrecTraits<T>::halo(P);
-    out[i] = (double)accel_m((T)r[i], T(0), S, Q, hc);
+    NoTally none;
+    out[i] = (double)accel_m((T)r[i], T(0), S, Q, hc, none);
 }
 
 int launch_force_probe(int precision, const DevProblem* d_prob, int stage, const double* d_r, int n,
@@ -396,17 +445,18 @@ size_t coef_smem_bytes(int precision, int n_steps)
     return (size_t)n_steps * C_COUNT * (precision == NU_FP64 ? sizeof(double) : sizeof(float));
 }
 
-template <typename T, int TPT>
+template <typename T, int TPT, bool COUNT>
 static int launch_t(int block, int grid, size_t smem, const DevProblem* d_probs, const int* d_prefix,
-                    int n_probs, int n_tiles, unsigned* d_counter, cudaStream_t s)
+                    int n_probs, int n_tiles, unsigned* d_counter, unsigned long long* d_tallies,
+                    cudaStream_t s)
 {
-    auto k = traj_kernel<T, TPT>;
+    auto k = traj_kernel<T, TPT, COUNT>;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return NU_ECUDA;
     }
-    k<<<grid, block, smem, s>>>(d_probs, d_prefix, n_probs, n_tiles, d_counter);
+    k<<<grid, block, smem, s>>>(d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies);
     if (cudaGetLastError() != cudaSuccess) return NU_ECUDA;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
@@ -419,17 +469,30 @@ int launch_traj(int precision, int tpt, int block, int grid, size_t smem, const 
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (precision == NU_FP64) {
-        if (tpt == 2) return launch_t<double, 2>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
-        return launch_t<double, 1>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
+        if (tpt == 2) return launch_t<double, 2, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+        return launch_t<double, 1, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
     }
-    if (tpt == 2) return launch_t<float, 2>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
-    return launch_t<float, 1>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
+    if (tpt == 2) return launch_t<float, 2, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+    return launch_t<float, 1, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+}
+
+int launch_traj_tally(int precision, int tpt, int block, int grid, size_t smem,
+                      const DevProblem* d_probs, const int* d_prefix, int n_probs, int n_tiles,
+                      unsigned* d_counter, unsigned long long* d_tallies, void* stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (precision == NU_FP64) {
+        if (tpt == 2) return launch_t<double, 2, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
+        return launch_t<double, 1, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
+    }
+    if (tpt == 2) return launch_t<float, 2, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
+    return launch_t<float, 1, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
 }
 
 template <typename T, int TPT>
 static int occ_t(int block, size_t smem, int* out)
 {
-    auto k = traj_kernel<T, TPT>;
+    auto k = traj_kernel<T, TPT, false>;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)

@@ -70,7 +70,14 @@ class nu_plan_info(C.Structure):
                 ("z_i", C.c_double), ("Ic", C.c_double), ("rho_bar0", C.c_double),
                 ("z_end", C.c_double), ("n_traj", C.c_longlong), ("h2d_bytes", C.c_longlong),
                 ("traj_steps", C.c_longlong),
-                ("device_bytes", C.c_longlong), ("n_tiles", C.c_int), ("tile", C.c_int)]
+                ("device_bytes", C.c_longlong), ("n_tiles", C.c_int), ("tile", C.c_int),
+                ("precision", C.c_int), ("n_steps", C.c_int)]
+
+
+class nu_tune_result(C.Structure):
+    _fields_ = [("block", C.c_int), ("tpt", C.c_int), ("best_ms", C.c_float),
+                ("from_cache", C.c_int), ("n_candidates", C.c_int),
+                ("cand_block", C.c_int * 8), ("cand_tpt", C.c_int * 8), ("cand_ms", C.c_float * 8)]
 
 
 _lib = None
@@ -102,6 +109,8 @@ def lib():
     L.nu_batch_run.argtypes = [vp, vp]
     L.nu_batch_kernel_ms.argtypes = [vp, P(C.c_float)]
     L.nu_batch_info.argtypes = [vp, P(C.c_int), P(C.c_longlong), P(C.c_longlong), P(C.c_int)]
+    L.nu_batch_branch_counts.argtypes = [vp, vp, P(C.c_longlong)]
+    L.nu_autotune.argtypes = [P(vp), C.c_int, vp, C.c_char_p, P(nu_tune_result)]
     L.nu_batch_destroy.argtypes = [vp]
     L.nu_batch_destroy.restype = None
     L.nu_profile_compute_noalloc.argtypes = [P(nu_cosmo), P(nu_halo), P(nu_relic), P(C.c_double),
@@ -116,7 +125,7 @@ def lib():
     for name in ("nu_profile_plan", "nu_profile_create", "nu_profile_run", "nu_profile_result",
                  "nu_profile_qi", "nu_profile_info", "nu_profile_force", "nu_batch_create",
                  "nu_batch_run",
-                 "nu_batch_kernel_ms", "nu_batch_info",
+                 "nu_batch_kernel_ms", "nu_batch_info", "nu_batch_branch_counts", "nu_autotune",
                  "nu_version"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -296,6 +305,21 @@ def nu_batch_info(b) -> dict:
     ts, hb = C.c_longlong(), C.c_longlong()
     _check(lib().nu_batch_info(b, C.byref(nt), C.byref(ts), C.byref(hb), C.byref(g)), "nu_batch_info")
     return {"n_tiles": nt.value, "traj_steps": ts.value, "h2d_bytes": hb.value, "grid": g.value}
+
+
+def nu_batch_branch_counts(b, stream=None):
+    counts = (C.c_longlong * 4)()
+    _check(lib().nu_batch_branch_counts(b, _stream_ptr(stream), counts), "nu_batch_branch_counts")
+    return [int(v) for v in counts]
+
+
+def nu_autotune(handles: Sequence, stream=None, cache_path: Optional[str] = None) -> dict:
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    r = nu_tune_result()
+    _check(lib().nu_autotune(arr, len(handles), _stream_ptr(stream),
+                             cache_path.encode() if cache_path else None, C.byref(r)), "nu_autotune")
+    return {"block": r.block, "tpt": r.tpt, "best_ms": r.best_ms, "from_cache": bool(r.from_cache),
+            "candidates": [(r.cand_block[i], r.cand_tpt[i], r.cand_ms[i]) for i in range(r.n_candidates)]}
 
 
 def nu_batch_destroy(b):

@@ -72,3 +72,65 @@ def test_batch_rejects_mixed_shapes():
     finally:
         nu.nu_profile_destroy(a)
         nu.nu_profile_destroy(c)
+
+
+def test_batch_tile_override_matches_handles_of_that_shape():
+    probs = [pb.replace(n_steps=120) for pb in W.batched_uneven(n_halos=6, seed=5)]
+    for block, tpt in ((128, 2), (512, 1)):
+        alone = []
+        for pb in probs:
+            h = nu.create(pb, block=block, tpt=tpt)
+            try:
+                nu.nu_profile_run(h)
+                alone.append(nu.nu_profile_result(h, pb.n_radii)[0])
+            finally:
+                nu.nu_profile_destroy(h)
+        hs = [nu.create(pb) for pb in probs]          # default shape 256 x 1
+        opts = nu.nu_opts()
+        opts.block, opts.tpt = block, tpt
+        b = nu.nu_batch_create(hs, opts)
+        try:
+            nu.nu_batch_run(b)
+            for h, pb, a in zip(hs, probs, alone):
+                assert np.array_equal(nu.nu_profile_result(h, pb.n_radii)[0], a)
+        finally:
+            nu.nu_batch_destroy(b)
+            for h in hs:
+                nu.nu_profile_destroy(h)
+
+
+def test_branch_counts_are_exact():
+    probs = [W.plain_small(precision=W.MIXED)[0].replace(n_steps=50),
+             W.plain_small(precision=W.MIXED)[0].replace(n_steps=50, M_h=0.0)]
+    for pb in probs:
+        h = nu.create(pb)
+        b = nu.nu_batch_create([h])
+        try:
+            c = nu.nu_batch_branch_counts(b)
+            assert sum(c) == 4 * pb.n_steps * pb.n_traj          # one trajectory per thread
+            if pb.M_h == 0.0:
+                assert c[0] == sum(c)                             # no halo: all beyond R
+            else:
+                assert min(c) > 0
+            # the counting launch leaves results alone; a normal run still works
+            nu.nu_batch_run(b)
+            assert np.all(np.isfinite(nu.nu_profile_result(h, pb.n_radii)[0]))
+        finally:
+            nu.nu_batch_destroy(b)
+            nu.nu_profile_destroy(h)
+
+
+def test_autotune_picks_the_fastest_and_caches(tmp_path):
+    probs = [pb.replace(n_steps=100) for pb in W.batched_uneven(n_halos=4, seed=9)]
+    hs = [nu.create(pb) for pb in probs]
+    try:
+        cache = str(tmp_path / "tune.jsonl")
+        r = nu.nu_autotune(hs, cache_path=cache)
+        assert not r["from_cache"] and len(r["candidates"]) == 6
+        assert r["best_ms"] == min(ms for _, _, ms in r["candidates"])
+        assert (r["block"], r["tpt"]) in [(b_, t_) for b_, t_, _ in r["candidates"]]
+        again = nu.nu_autotune(hs, cache_path=cache)
+        assert again["from_cache"] and (again["block"], again["tpt"]) == (r["block"], r["tpt"])
+    finally:
+        for h in hs:
+            nu.nu_profile_destroy(h)
