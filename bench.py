@@ -181,9 +181,17 @@ def bench_ours(args):
 
     with torch.cuda.stream(stream):
         hs = [nu.create(pb, stream=stream) for pb in problems]
+    # launch shape: autotuned (untimed) unless given as BLOCKxTPT
+    if args.shape == "auto":
+        tune = nu.nu_autotune(hs, stream)
+        block, tpt = tune["block"], tune["tpt"]
+    else:
+        block, tpt = (int(v) for v in args.shape.lower().split("x"))
+        tune = None
     opts = nu.nu_opts()
     opts.flags = nu.NU_FLAG_TIMING
     opts.stream = stream.cuda_stream
+    opts.block, opts.tpt = block, tpt
     batch = nu.nu_batch_create(hs, opts)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
@@ -268,7 +276,7 @@ def bench_ours(args):
     peak = fp32_peak_tflops(peak_mhz)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "traj_kernel<float,1>", "kernel_ms": kms,
+                "kernel": f"traj_kernel<float,{tpt}>", "kernel_ms": kms,
                 "flops_per_launch": flops, "flops_per_traj_step": flops / traj_steps,
                 "branch_counts": {"beyond_R": counts[0], "shell": counts[1],
                                   "nfw_poly": counts[2], "nfw_log": counts[3]},
@@ -296,8 +304,10 @@ def bench_ours(args):
             "config": {"workload": WORKLOAD_USED, "traj_steps_per_step": traj_steps,
                        "precision": "mixed: FP32 state/force, FP64 tables and sums",
                        "l2": "flushed (256 MiB write) between timed steps",
-                       "launch": f"one persistent batched launch per step: grid {grid} CTAs x 256 "
-                                 "threads, 1 trajectory/thread",
+                       "launch": f"one persistent batched launch per step: grid {grid} CTAs x {block} "
+                                 f"threads, {tpt} trajectories/thread",
+                       "autotune": (None if tune is None else
+                                    {f"{b_}x{t_}": round(ms, 4) for b_, t_, ms in tune["candidates"]}),
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": traj_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
@@ -317,6 +327,8 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--shape", default="auto",
+                    help="tile shape BLOCKxTPT (e.g. 256x1), or auto to run the autotuner first")
     ap.add_argument("--case", choices=("full", "small"), default="full",
                     help="small: one mass x 8 radii of the same workload, for profiler captures")
     args = ap.parse_args()
