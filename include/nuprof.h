@@ -254,16 +254,18 @@ NU_API void nu_batch_destroy(nu_batch* b);
  * (never run), NU_ECUDA. */
 NU_API int nu_batch_kernel_ms(nu_batch* b, float* ms);
 
-/* Exact branch statistics of one run of the batch, from a counting variant of
- * the trajectory kernel (launched once, synchronously, on `stream`; it does not
- * write the requests' results): counts[0] force evaluations beyond R (gradient
- * exactly zero), counts[1] in the compensating shell, counts[2] in the NFW part
- * with I(y) on its polynomial branch (y < 1), counts[3] on its logarithm
- * branch.  Every trajectory slot that was integrated is counted: with one
- * trajectory per thread that is exactly the requests' trajectories, with two
- * a padding slot of a ragged tile runs beside a real one.  The force is data dependent (App. A has three branches), so these
- * counts turn the work of a run into an exact algorithmic flop count.
- * Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
+/* Exact work statistics of one run of the batch, from a counting variant of
+ * the trajectory kernel (launched once, synchronously, on `stream`; its
+ * results are those of a normal run).  For unfinished trajectories only:
+ * counts[0] force evaluations beyond R (gradient exactly zero), counts[1] in
+ * the compensating shell, counts[2] in the NFW part with I(y) on its
+ * polynomial branch (y < 1), counts[3] on its logarithm branch, counts[4]
+ * trajectory-steps integrated.  A trajectory is finished once it lies beyond R
+ * and recedes along the integration direction: no later step changes its
+ * velocity, so its remaining steps are not needed work (its warp stops when
+ * all of its lanes are finished).  The force is data dependent (App. A has
+ * three branches), so these counts turn one run into an exact algorithmic flop
+ * count.  counts must hold 5 values.  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
 NU_API int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts);
 
 /* Launch-shape autotuner: times the batch of requests `hs` with each candidate

@@ -128,7 +128,7 @@ struct nu_batch {
     unsigned* d_ctrl = nullptr;
     long long h2d_bytes = 0;
     long long traj_steps = 0;
-    unsigned long long* d_tallies = nullptr;   // [4], allocated at the first count
+    unsigned long long* d_tallies = nullptr;   // [5], allocated at the first count
     bool use_graph = false;
     bool timing = false;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -637,12 +637,14 @@ int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts)
 {
     if (!b || !counts) return NU_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (!b->d_tallies && cudaMalloc(&b->d_tallies, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+    constexpr int kTallies = 5;
+    if (!b->d_tallies &&
+        cudaMalloc(&b->d_tallies, kTallies * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         b->d_tallies = nullptr;
         return NU_ENOMEM;
     }
-    unsigned long long host[4] = {0, 0, 0, 0};
+    unsigned long long host[kTallies] = {0, 0, 0, 0, 0};
     int rc = NU_OK;
     if (cudaMemsetAsync(b->d_tallies, 0, sizeof(host), s) != cudaSuccess ||
         cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess)
@@ -658,7 +660,7 @@ int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts)
         cudaGetLastError();
         return rc;
     }
-    for (int k = 0; k < 4; ++k) counts[k] = (long long)host[k];
+    for (int k = 0; k < kTallies; ++k) counts[k] = (long long)host[k];
     return NU_OK;
 }
 

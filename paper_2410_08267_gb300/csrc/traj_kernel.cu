@@ -107,13 +107,22 @@ struct HaloF64 { double invIc, invR3, R2; };
 // Branch tallies of force evaluations, kept only by the counting variant of the
 // kernel (used once, untimed, to turn the data-dependent work into an exact
 // algorithmic flop count): beyond R, shell, NFW part on the polynomial branch
-// of I(y), NFW part on the logarithm branch.
+// of I(y), NFW part on the logarithm branch, and the trajectory-steps of
+// unfinished trajectories.  Steps that a finished trajectory runs only because
+// its warp is still busy are not counted (they are not needed work).
 struct NoTally {
     __device__ __forceinline__ void add(int) {}
+    __device__ __forceinline__ void set_live(bool) {}
 };
 struct Tally {
-    unsigned n[4] = {0u, 0u, 0u, 0u};
-    __device__ __forceinline__ void add(int k) { ++n[k]; }
+    unsigned n[5] = {0u, 0u, 0u, 0u, 0u};   // 4 branches + live trajectory-steps
+    bool live = true;                       // only unfinished trajectories count
+    __device__ __forceinline__ void add(int k) { n[k] += live ? 1u : 0u; }
+    __device__ __forceinline__ void set_live(bool v)
+    {
+        live = v;
+        n[4] += v ? 1u : 0u;
+    }
 };
 
 // The compensated halo's gradient vanishes beyond R, and the NFW term only
@@ -302,12 +311,12 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         T x[TPT], y[TPT], vx[TPT], vy[TPT];
         int tj[TPT], tk[TPT];
         bool act[TPT];
-        bool any = false;
+        bool done = true;            // every trajectory of this lane is finished
 #pragma unroll
         for (int i = 0; i < TPT; ++i) {
             const int t = tis * P.tile + i * blockDim.x + threadIdx.x;
             act[i] = t < n_seg;
-            any |= act[i];
+            done &= !act[i];
             const int tt = act[i] ? t : 0;
             tj[i] = tt / n_mu;
             tk[i] = tt - tj[i] * n_mu;
@@ -318,15 +327,34 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             vy[i] = v0 * reinterpret_cast<const T*>(P.smu)[tk[i]];
         }
 
-        if (any) {
+        // A trajectory beyond R whose position recedes along the integration
+        // direction (x . v <= 0: the backward step moves it along -v) never
+        // re-enters: the gradient is exactly zero there (mass compensation),
+        // so every later step leaves v unchanged and q_i depends on v alone.
+        // A warp stops integrating once all of its lanes are in that state
+        // (padding lanes of a ragged tile start finished).  All lanes of the
+        // warp reach the vote, so the full mask is valid.
+        {
             for (int n = 0; n < n_steps; ++n) {
+                bool fin = true, fin_i[TPT];
+#pragma unroll
+                for (int i = 0; i < TPT; ++i) {
+                    fin_i[i] = !act[i] || (fma(x[i], x[i], y[i] * y[i]) >= hc.R2 &&
+                                           fma(x[i], vx[i], y[i] * vy[i]) <= T(0));
+                    fin &= fin_i[i];
+                }
+                done |= fin;
+                if (__all_sync(0xffffffffu, done)) break;
                 T c[C_COUNT];
                 const float4* c4 = reinterpret_cast<const float4*>(s_coef + (size_t)n * C_COUNT);
 #pragma unroll
                 for (int q = 0; q < (int)(C_COUNT * sizeof(T) / 16); ++q)
                     reinterpret_cast<float4*>(c)[q] = c4[q];
 #pragma unroll
-                for (int i = 0; i < TPT; ++i) rk4_step<T, Ctr>(x[i], y[i], vx[i], vy[i], c, hc, ctr);
+                for (int i = 0; i < TPT; ++i) {
+                    ctr.set_live(!fin_i[i] && !done);
+                    rk4_step<T, Ctr>(x[i], y[i], vx[i], vy[i], c, hc, ctr);
+                }
             }
         }
 
@@ -393,11 +421,8 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         // the next iteration's first __syncthreads orders s_tile/s_last reuse
     }
     if constexpr (COUNT) {
-        // inactive padding lanes integrate a copy of trajectory 0; the tallies
-        // count every lane that ran, so the host subtracts nothing: the padding
-        // work is real work the kernel did
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 5; ++k) {
             unsigned long long v = ctr.n[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

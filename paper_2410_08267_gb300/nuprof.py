@@ -308,7 +308,7 @@ def nu_batch_info(b) -> dict:
 
 
 def nu_batch_branch_counts(b, stream=None):
-    counts = (C.c_longlong * 4)()
+    counts = (C.c_longlong * 5)()
     _check(lib().nu_batch_branch_counts(b, _stream_ptr(stream), counts), "nu_batch_branch_counts")
     return [int(v) for v in counts]
 

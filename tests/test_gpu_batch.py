@@ -107,9 +107,13 @@ def test_branch_counts_are_exact():
         b = nu.nu_batch_create([h])
         try:
             c = nu.nu_batch_branch_counts(b)
-            assert sum(c) == 4 * pb.n_steps * pb.n_traj          # one trajectory per thread
+            # four force evaluations per integrated step of an unfinished trajectory
+            assert sum(c[:4]) == 4 * c[4] and 0 < c[4] <= pb.n_steps * pb.n_traj
             if pb.M_h == 0.0:
-                assert c[0] == sum(c)                             # no halo: all beyond R
+                assert c[0] == sum(c[:4])                         # no halo: all beyond R
+                # every trajectory starting with mu <= 0 recedes from the start
+                mu = np.polynomial.legendre.leggauss(pb.n_mu)[0]
+                assert c[4] <= pb.n_steps * pb.n_radii * pb.n_q * int((mu > 0).sum())
             else:
                 assert min(c) > 0
             # the counting launch leaves results alone; a normal run still works
