@@ -329,6 +329,22 @@ NU_API int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* halo
                                       const nu_pgrid* p_grid, const nu_opts* opts,
                                       double* n_over_nbar, double* err_est, void* stream);
 
+/* Measured arithmetic throughput of the current GPU (the denominators of the
+ * trajectory kernel's roofline, an FP32 ALU-bound path): scalar FP32 FMA and
+ * packed FP32x2 FMA in TFLOP/s (FMA = 2 flops), and the special-function
+ * unit's reciprocal square root and base-2 logarithm in Gop/s.  Each kernel
+ * runs 8 independent chains per thread on 8 CTAs of 256 threads per SM, timed
+ * with CUDA events on `stream` after one warm-up.  Errors: NU_EINVAL, NU_ECUDA. */
+typedef struct nu_peaks {
+    double ffma_tflops;
+    double ffma2_tflops;
+    double rsqrt_gops;
+    double lg2_gops;
+    int sm_count;
+    int clock_mhz_nominal;   /* cudaDevAttrClockRate / 1000 */
+} nu_peaks;
+NU_API int nu_measure_peaks(void* stream, nu_peaks* out);
+
 /* Launch counters: kernels launched by the library since load (all handles). */
 NU_API long long nu_kernel_launches(void);
 

@@ -74,6 +74,12 @@ class nu_plan_info(C.Structure):
                 ("precision", C.c_int), ("n_steps", C.c_int)]
 
 
+class nu_peaks(C.Structure):
+    _fields_ = [("ffma_tflops", C.c_double), ("ffma2_tflops", C.c_double),
+                ("rsqrt_gops", C.c_double), ("lg2_gops", C.c_double),
+                ("sm_count", C.c_int), ("clock_mhz_nominal", C.c_int)]
+
+
 class nu_tune_result(C.Structure):
     _fields_ = [("block", C.c_int), ("tpt", C.c_int), ("best_ms", C.c_float),
                 ("from_cache", C.c_int), ("n_candidates", C.c_int),
@@ -117,6 +123,8 @@ def lib():
                                              C.c_int, P(nu_pgrid), P(nu_opts), P(C.c_double),
                                              P(C.c_double), vp]
     L.nu_profile_compute_noalloc.restype = C.c_int
+    L.nu_measure_peaks.argtypes = [vp, P(nu_peaks)]
+    L.nu_measure_peaks.restype = C.c_int
     L.nu_kernel_launches.argtypes = []
     L.nu_kernel_launches.restype = C.c_longlong
     L.nu_strerror.argtypes = [C.c_int]
@@ -208,6 +216,12 @@ def strerror(code: int) -> str:
 
 
 nu_strerror = strerror
+
+
+def nu_measure_peaks(stream=None) -> dict:
+    p = nu_peaks()
+    _check(lib().nu_measure_peaks(_stream_ptr(stream), C.byref(p)), "nu_measure_peaks")
+    return {k: getattr(p, k) for k, _ in nu_peaks._fields_}
 
 
 def nu_kernel_launches() -> int:
