@@ -146,7 +146,9 @@ typedef struct nu_opts {
     double z_end;        /* end of the backward integration; <= 0 -> the paper's z_i */
     int radii_unit;      /* NU_RADII_*                                            */
     int block;           /* threads per CTA: 0 (default 256) or 64..512, multiple of 32 */
-    int tpt;             /* trajectories per thread: 0 (default 1), 1 or 2       */
+    int tpt;             /* trajectories per thread: 0 (default 1), 1, 2, or 3 =
+                            two per thread in packed FP32x2 arithmetic (mixed
+                            precision, n_steps <= 1760; results bitwise those of 2) */
     int flags;           /* NU_FLAG_*                                             */
     nu_alloc_fn alloc;
     nu_free_fn free;
@@ -270,7 +272,8 @@ NU_API int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts);
 
 /* Launch-shape autotuner: times the batch of requests `hs` with each candidate
  * tile shape (threads per CTA x trajectories per thread: 128x1, 256x1, 512x1,
- * 64x2, 128x2, 256x2; one warm-up and the median of three runs) and reports the
+ * 128x2, 256x2, and for mixed precision the packed 128x3, 256x3, 512x3; one
+ * warm-up and the median of three runs) and reports the
  * fastest.  With cache_path != NULL, a JSON-lines cache keyed by GPU name,
  * precision, step-count and trajectory-count buckets (powers of two) is read
  * first and appended to after tuning.  Results of different shapes agree to

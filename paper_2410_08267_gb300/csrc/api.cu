@@ -150,7 +150,7 @@ int plan_common(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* reli
     rc = derive(*cosmo, *halo, o, d);
     if (rc != NU_OK) return rc;
     const long long seg = (long long)grid->n_q * grid->n_mu;
-    const int tile = o.block * o.tpt;
+    const int tile = o.block * traj_per_thread(o.tpt);
     tiles_per_seg = (int)((seg + tile - 1) / tile);
     std::memset(&info, 0, sizeof(info));
     info.R_kpc = d.R;
@@ -248,7 +248,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     h->n_radii = n_radii;
     h->tiles_per_seg = tps;
     h->n_tiles = info.n_tiles;
-    h->smem = coef_smem_bytes(o.precision, o.n_steps);
+    h->smem = coef_smem_bytes(o.precision, o.n_steps, o.tpt);
 
     // ---- host tables (FP64) ----
     const int nq = p_grid->n_q, nmu = p_grid->n_mu, N = o.n_steps;
@@ -278,6 +278,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     const size_t o_prob = carve(sizeof(DevProblem));
     const size_t o_pref = carve(2 * sizeof(int));
     const size_t o_coef = carve((size_t)N * C_COUNT * sz);
+    const size_t o_coef2 = fp64 ? 0 : carve((size_t)N * C_COUNT * 2 * sizeof(float));
     const size_t o_x0 = carve((size_t)n_radii * sz);
     const size_t o_v0 = carve((size_t)nq * sz);
     const size_t o_mu = carve((size_t)nmu * sz);
@@ -303,6 +304,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     DevProblem& P = h->hdp;
     std::memset(&P, 0, sizeof(P));
     P.coef = base + o_coef;
+    P.coef2 = fp64 ? nullptr : base + o_coef2;
     P.x0 = base + o_x0;
     P.v0 = base + o_v0;
     P.mu = base + o_mu;
@@ -329,7 +331,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     P.n_mu = nmu;
     P.n_steps = N;
     P.tiles_per_seg = tps;
-    P.tile = o.block * o.tpt;
+    P.tile = o.block * traj_per_thread(o.tpt);
     P.precision = o.precision;
 
     std::vector<unsigned char> stage(upload_end, 0);
@@ -344,6 +346,8 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
         put<double>(stage, o_smu, smu.data(), nmu);
     } else {
         put<float>(stage, o_coef, coef.data(), coef.size());
+        float* c2 = reinterpret_cast<float*>(stage.data() + o_coef2);
+        for (size_t i = 0; i < coef.size(); ++i) c2[2 * i] = c2[2 * i + 1] = (float)coef[i];
         put<float>(stage, o_x0, x0.data(), n_radii);
         put<float>(stage, o_v0, v0.data(), nq);
         put<float>(stage, o_mu, mu.data(), nmu);
@@ -490,7 +494,7 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
     const int want_block = opts ? opts->block : 0;
     const int want_tpt = opts ? opts->tpt : 0;
     if ((want_block != 0 && (want_block < 64 || want_block > 512 || want_block % 32 != 0)) ||
-        (want_tpt != 0 && want_tpt != 1 && want_tpt != 2))
+        (want_tpt != 0 && want_tpt != 1 && want_tpt != 2 && want_tpt != kTptPacked))
         return NU_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!hs[i]) return NU_EINVAL;
@@ -503,10 +507,14 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
                    (!want_block && o.block != b->block)) {
             return NU_EINVAL;
         }
-        b->smem = std::max(b->smem, hs[i]->smem);
         b->hs.push_back(hs[i]);
     }
-    const int tile = b->block * b->tpt;
+    if (b->tpt == kTptPacked && b->precision != NU_MIXED) return NU_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (b->tpt == kTptPacked && hs[i]->opts.n_steps > 1760) return NU_ENOTSUP;
+        b->smem = std::max(b->smem, coef_smem_bytes(b->precision, hs[i]->opts.n_steps, b->tpt));
+    }
+    const int tile = b->block * traj_per_thread(b->tpt);
     std::vector<DevProblem> descs(n);
     std::vector<int> prefix(n + 1, 0);
     for (int i = 0; i < n; ++i) {

@@ -26,7 +26,7 @@ namespace {
 struct Shape {
     int block, tpt;
 };
-const Shape kShapes[] = {{128, 1}, {256, 1}, {512, 1}, {64, 2}, {128, 2}, {256, 2}};
+const Shape kShapes[] = {{128, 1}, {256, 1}, {512, 1}, {128, 2}, {256, 2}, {128, 3}, {256, 3}, {512, 3}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 int bucket_pow2(long long v)
@@ -105,6 +105,7 @@ extern "C" int nu_autotune(nu_profile* const* hs, int n, void* stream, const cha
     long long traj = 0;
     int max_steps = 0, precision = -1;
     for (int i = 0; i < n; ++i) {
+        // (the packed shape, tpt 3, is tried for mixed precision only)
         if (!hs[i] || nu_profile_info(hs[i], &info) != NU_OK) return NU_EINVAL;
         if (precision >= 0 && info.precision != precision) return NU_EINVAL;
         precision = info.precision;
@@ -123,7 +124,9 @@ extern "C" int nu_autotune(nu_profile* const* hs, int n, void* stream, const cha
         return NU_OK;
     }
     float best = 1e30f;
+    int slot = 0;
     for (int c = 0; c < kNumShapes; ++c) {
+        if (kShapes[c].tpt == 3 && (precision != NU_MIXED || max_steps > 1760)) continue;
         nu_opts o;
         std::memset(&o, 0, sizeof(o));
         o.block = kShapes[c].block;
@@ -142,9 +145,10 @@ extern "C" int nu_autotune(nu_profile* const* hs, int n, void* stream, const cha
         nu_batch_destroy(b);
         if (rc != NU_OK) return rc;
         std::sort(t, t + 3);
-        out->cand_block[c] = o.block;
-        out->cand_tpt[c] = o.tpt;
-        out->cand_ms[c] = t[1];
+        out->cand_block[slot] = o.block;
+        out->cand_tpt[slot] = o.tpt;
+        out->cand_ms[slot] = t[1];
+        ++slot;
         if (t[1] < best) {
             best = t[1];
             out->block = o.block;
@@ -152,7 +156,7 @@ extern "C" int nu_autotune(nu_profile* const* hs, int n, void* stream, const cha
             out->best_ms = t[1];
         }
     }
-    out->n_candidates = kNumShapes;
+    out->n_candidates = slot;
     if (cache_path) cache_store(cache_path, key, *out);
     return NU_OK;
 }

@@ -44,7 +44,10 @@ int validate(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
     if (o->radii_unit != NU_RADII_KPC && o->radii_unit != NU_RADII_R200) return NU_EINVAL;
     if (o->radii_unit == NU_RADII_R200 && halo->M_h == 0.0) return NU_EINVAL;
     if (o->block < 64 || o->block > 512 || (o->block % 32) != 0) return NU_EINVAL;
-    if (o->tpt != 1 && o->tpt != 2) return NU_EINVAL;
+    if (o->tpt != 1 && o->tpt != 2 && o->tpt != kTptPacked) return NU_EINVAL;
+    if (o->tpt == kTptPacked && o->precision != NU_MIXED) return NU_EINVAL;
+    // the packed path stages 128 bytes per step in shared memory
+    if (o->tpt == kTptPacked && o->n_steps > 1760) return NU_ENOTSUP;
     long long ntraj = (long long)g->n_q * g->n_mu;
     if (ntraj > (1LL << 30) || (long long)n_radii * ntraj > (1LL << 40)) return NU_EINVAL;
     return NU_OK;
@@ -255,6 +258,7 @@ long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_m
     b += align256(sizeof(DevProblem));
     b += align256(2 * sizeof(int));                             // tile prefix
     b += align256((size_t)n_steps * C_COUNT * sz);               // coefficient table
+    if (precision == NU_MIXED) b += align256((size_t)n_steps * C_COUNT * 2 * sizeof(float));
     b += align256((size_t)n_radii * sz);                         // x0
     b += align256((size_t)n_q * sz);                             // v0
     b += 2 * align256((size_t)n_mu * sz);                        // mu, sin psi

@@ -65,6 +65,7 @@ long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_m
 // Device-visible description of one request (POD, lives in device memory).
 struct DevProblem {
     const void* coef;       // [n_steps][16] float (mixed) or double (fp64)
+    const void* coef2;      // [n_steps][16][2] float, every value twice (mixed; packed path)
     const void* x0;         // [n_radii] start radius, kpc
     const void* v0;         // [n_q] start speed, km/s
     const void* mu;         // [n_mu] cos psi
@@ -100,7 +101,11 @@ int max_ctas_per_sm(int precision, int tpt, int block, size_t smem_bytes, int* o
 // Smallest tile (block 64 x 1 trajectory): request buffers of tile sums are
 // sized for it, so a batch may run any tile shape over existing requests.
 constexpr int kMinTile = 64;
-size_t coef_smem_bytes(int precision, int n_steps);
+size_t coef_smem_bytes(int precision, int n_steps, int tpt);
+// Trajectories per thread of a tile shape: tpt 3 is two trajectories per
+// thread in packed FP32x2 arithmetic (mixed precision only).
+inline int traj_per_thread(int tpt) { return tpt == 3 ? 2 : tpt; }
+constexpr int kTptPacked = 3;
 int launch_force_probe(int precision, const DevProblem* d_prob, int stage, const double* d_r, int n,
                        double* d_out, void* stream);
 void count_launch();

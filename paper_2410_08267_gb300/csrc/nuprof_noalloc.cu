@@ -188,6 +188,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     nu_opts o;
     resolve_opts(opts, o);
     if (o.flags != 0) return NU_EINVAL;
+    if (o.tpt == kTptPacked) return NU_ENOTSUP;   // the packed table is not staged here
     int rc = validate(cosmo, halo, relic, radii, n_radii, p_grid, &o);
     if (rc != NU_OK) return rc;
     Derived d;
@@ -317,7 +318,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     put_into<double>(st, o_wmu, wmu, nmu);
 
     int per_sm = 0, sms = 0, devid = 0;
-    const size_t smem = coef_smem_bytes(o.precision, N);
+    const size_t smem = coef_smem_bytes(o.precision, N, o.tpt);
     rc = max_ctas_per_sm(o.precision, o.tpt, o.block, smem, &per_sm);
     if (rc != NU_OK) return rc;
     if (cudaGetDevice(&devid) != cudaSuccess ||

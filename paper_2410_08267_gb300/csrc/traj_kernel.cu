@@ -218,45 +218,183 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
 // One classical RK4 step of size -h for one trajectory (Eq. eoms in ln a).
-// c points at the step's 16 coefficients (see CoefSlot).
+// c points at the step's 16 coefficients (see CoefSlot).  Every product-sum
+// is an explicit fused multiply-add, so the packed two-trajectory variant
+// below performs exactly the same roundings.
 template <typename T, class Ctr>
 __device__ __forceinline__ void rk4_step(T& x, T& y, T& vx, T& vy, const T* c,
                                          const typename PrecTraits<T>::Halo& hc, Ctr& ctr)
 {
     const T m1 = accel_m(x, y, c[C_S0], c[C_Q0], hc, ctr);
     const T p1 = c[C_B1] * m1;
-    const T X2 = x + c[C_MA1] * vx, Y2 = y + c[C_MA1] * vy;
-    const T VX2 = vx + p1 * x, VY2 = vy + p1 * y;
+    const T X2 = fmaT(c[C_MA1], vx, x), Y2 = fmaT(c[C_MA1], vy, y);
+    const T VX2 = fmaT(p1, x, vx), VY2 = fmaT(p1, y, vy);
 
     const T m2 = accel_m(X2, Y2, c[C_S1], c[C_Q1], hc, ctr);
     const T p2 = c[C_B2] * m2;
-    const T X3 = x + c[C_MA2] * VX2, Y3 = y + c[C_MA2] * VY2;
-    const T VX3 = vx + p2 * X2, VY3 = vy + p2 * Y2;
+    const T X3 = fmaT(c[C_MA2], VX2, x), Y3 = fmaT(c[C_MA2], VY2, y);
+    const T VX3 = fmaT(p2, X2, vx), VY3 = fmaT(p2, Y2, vy);
 
     const T m3 = accel_m(X3, Y3, c[C_S1], c[C_Q1], hc, ctr);
     const T p3 = c[C_B3] * m3;
-    const T X4 = x + c[C_MA3] * VX3, Y4 = y + c[C_MA3] * VY3;
-    const T VX4 = vx + p3 * X3, VY4 = vy + p3 * Y3;
+    const T X4 = fmaT(c[C_MA3], VX3, x), Y4 = fmaT(c[C_MA3], VY3, y);
+    const T VX4 = fmaT(p3, X3, vx), VY4 = fmaT(p3, Y3, vy);
 
     const T m4 = accel_m(X4, Y4, c[C_S2], c[C_Q2], hc, ctr);
     const T p4 = c[C_B4] * m4;
 
     // x' = x - (h/6) (A_a v + 2 A_m V2 + 2 A_m V3 + A_b V4)
-    const T nx = x + c[C_W0] * vx + c[C_W1] * (VX2 + VX3) + c[C_W2] * VX4;
-    const T ny = y + c[C_W0] * vy + c[C_W1] * (VY2 + VY3) + c[C_W2] * VY4;
+    const T nx = fmaT(c[C_W2], VX4, fmaT(c[C_W1], VX2 + VX3, fmaT(c[C_W0], vx, x)));
+    const T ny = fmaT(c[C_W2], VY4, fmaT(c[C_W1], VY2 + VY3, fmaT(c[C_W0], vy, y)));
     // v' = v + (h/6) (BF_a m1 x + 2 BF_m m2 X2 + 2 BF_m m3 X3 + BF_b m4 X4)
     const T p2x2 = p2 + p2;
     const T third = T(1) / T(3);
-    const T nvx = vx + (p1 * x + p2x2 * X2 + p3 * X3) * third + p4 * X4;
-    const T nvy = vy + (p1 * y + p2x2 * Y2 + p3 * Y3) * third + p4 * Y4;
+    const T tx = fmaT(p3, X3, fmaT(p2x2, X2, p1 * x));
+    const T ty = fmaT(p3, Y3, fmaT(p2x2, Y2, p1 * y));
+    const T nvx = fmaT(p4, X4, fmaT(tx, third, vx));
+    const T nvy = fmaT(p4, Y4, fmaT(ty, third, vy));
     x = nx;
     y = ny;
     vx = nvx;
     vy = nvy;
 }
 
-template <typename T, int TPT, bool COUNT>
+// ---------------------------------------------------------------------------
+// Packed FP32x2 path: two trajectories per thread held as register pairs, every
+// arithmetic operation issued as one f32x2 instruction (fma/mul/add.rn.f32x2).
+// Each component sees exactly the operations of the scalar path above, in the
+// same order, so the results are bitwise those of the two-trajectory scalar
+// kernel; only selects, comparisons and the special functions stay scalar.
+// The coefficients come from a table with every value stored twice ({c, c}),
+// so a 16-byte shared load yields two ready operand pairs.
+// ---------------------------------------------------------------------------
+struct f2 {
+    unsigned long long v;
+};
+
+__device__ __forceinline__ f2 pk(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float f2lo(f2 a)
+{
+    float l, h;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(a.v));
+    return l;
+}
+__device__ __forceinline__ float f2hi(f2 a)
+{
+    float l, h;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(a.v));
+    return h;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 dup(float a) { return pk(a, a); }
+
+struct HaloX2 {
+    f2 invIc, neg_invR3;
+    float R2;
+};
+
+// I(y) on the polynomial branch for both lanes (see nfw_I).
+__device__ __forceinline__ f2 nfw_I_poly_x2(f2 y)
+{
+    f2 p = dup(-1.933632977e-02f);
+    p = fma2(p, y, dup(1.171014905e-01f));
+    p = fma2(p, y, dup(-3.268344104e-01f));
+    p = fma2(p, y, dup(5.741083622e-01f));
+    p = fma2(p, y, dup(-7.448884845e-01f));
+    p = fma2(p, y, dup(8.059346676e-01f));
+    p = fma2(p, y, dup(-7.959684730e-01f));
+    p = fma2(p, y, dup(7.496873736e-01f));
+    p = fma2(p, y, dup(-6.666569710e-01f));
+    p = fma2(p, y, dup(4.999999404e-01f));
+    return mul2(mul2(y, y), p);
+}
+
+// m = Mhat/r^3 for both lanes, the values of accel_m (FP32) lane by lane.
+__device__ __forceinline__ f2 accel_m_x2(f2 x, f2 y, f2 S, f2 Q, const HaloX2& hc)
+{
+    const f2 r2 = fma2(x, x, mul2(y, y));
+    const float r2a = f2lo(r2), r2b = f2hi(r2);
+    const f2 rinv = pk(rsqrt_approx(fmaxf(r2a, 1e-20f)), rsqrt_approx(fmaxf(r2b, 1e-20f)));
+    const f2 rinv3 = mul2(mul2(rinv, rinv), rinv);
+    const f2 ys = mul2(mul2(r2, rinv), S);
+    const float ya = f2lo(ys), yb = f2hi(ys);
+    f2 I;
+    if (ya < 1.0f && yb < 1.0f) I = nfw_I_poly_x2(ys);
+    else I = pk(nfw_I(ya), nfw_I(yb));
+    const f2 Iq = mul2(I, hc.invIc);
+    const float sa = r2a < f2lo(Q) ? f2lo(Iq) : 1.0f;
+    const float sb = r2b < f2hi(Q) ? f2hi(Iq) : 1.0f;
+    const f2 m = fma2(pk(sa, sb), rinv3, hc.neg_invR3);
+    return pk(r2a < hc.R2 ? f2lo(m) : 0.0f, r2b < hc.R2 ? f2hi(m) : 0.0f);
+}
+
+// rk4_step for two trajectories at once; cq points at the step's 8 x 16 bytes
+// of the duplicated table (slot j -> floats 2j, 2j+1).
+__device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const ulonglong2* cq,
+                                            const HaloX2& hc)
+{
+    const ulonglong2 q0 = cq[0], q1 = cq[1], q2 = cq[2], q3 = cq[3];
+    const ulonglong2 q4 = cq[4], q5 = cq[5], q6 = cq[6], q7 = cq[7];
+    const f2 MA1{q0.x}, MA2{q0.y}, MA3{q1.x}, B1{q1.y}, B2{q2.x}, B3{q2.y}, B4{q3.x}, W0{q3.y};
+    const f2 W1{q4.x}, W2{q4.y}, S0{q5.x}, S1{q5.y}, S2{q6.x}, Q0{q6.y}, Q1{q7.x}, Q2{q7.y};
+
+    const f2 m1 = accel_m_x2(x, y, S0, Q0, hc);
+    const f2 p1 = mul2(B1, m1);
+    const f2 X2 = fma2(MA1, vx, x), Y2 = fma2(MA1, vy, y);
+    const f2 VX2 = fma2(p1, x, vx), VY2 = fma2(p1, y, vy);
+
+    const f2 m2 = accel_m_x2(X2, Y2, S1, Q1, hc);
+    const f2 p2 = mul2(B2, m2);
+    const f2 X3 = fma2(MA2, VX2, x), Y3 = fma2(MA2, VY2, y);
+    const f2 VX3 = fma2(p2, X2, vx), VY3 = fma2(p2, Y2, vy);
+
+    const f2 m3 = accel_m_x2(X3, Y3, S1, Q1, hc);
+    const f2 p3 = mul2(B3, m3);
+    const f2 X4 = fma2(MA3, VX3, x), Y4 = fma2(MA3, VY3, y);
+    const f2 VX4 = fma2(p3, X3, vx), VY4 = fma2(p3, Y3, vy);
+
+    const f2 m4 = accel_m_x2(X4, Y4, S2, Q2, hc);
+    const f2 p4 = mul2(B4, m4);
+
+    const f2 nx = fma2(W2, VX4, fma2(W1, add2(VX2, VX3), fma2(W0, vx, x)));
+    const f2 ny = fma2(W2, VY4, fma2(W1, add2(VY2, VY3), fma2(W0, vy, y)));
+    const f2 p2x2 = add2(p2, p2);
+    const f2 third = dup(1.0f / 3.0f);
+    const f2 tx = fma2(p3, X3, fma2(p2x2, X2, mul2(p1, x)));
+    const f2 ty = fma2(p3, Y3, fma2(p2x2, Y2, mul2(p1, y)));
+    vx = fma2(p4, X4, fma2(tx, third, vx));
+    vy = fma2(p4, Y4, fma2(ty, third, vy));
+    x = nx;
+    y = ny;
+}
+
+template <typename T, int TPT, bool COUNT, bool PACKED = false>
 __global__ void __launch_bounds__(512)
 traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_prefix,
             int n_probs, int n_tiles, unsigned* __restrict__ tile_counter,
@@ -291,9 +429,9 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         const int n_steps = P.n_steps;
 
         if (lo != cur) {   // stage this request's coefficient table (uniform branch)
-            const float4* src = reinterpret_cast<const float4*>(P.coef);
+            const float4* src = reinterpret_cast<const float4*>(PACKED ? P.coef2 : P.coef);
             float4* dst = reinterpret_cast<float4*>(s_coef);
-            const int n16 = (int)((size_t)n_steps * C_COUNT * sizeof(T) / 16);
+            const int n16 = (int)((size_t)n_steps * C_COUNT * sizeof(T) * (PACKED ? 2 : 1) / 16);
             for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(&src[i]);
             __syncthreads();
             cur = lo;
@@ -345,6 +483,20 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                 }
                 done |= fin;
                 if (__all_sync(0xffffffffu, done)) break;
+                if constexpr (PACKED) {
+                    static_assert(TPT == 2, "packed path holds two trajectories");
+                    f2 X = pk(x[0], x[1]), Y = pk(y[0], y[1]);
+                    f2 VX = pk(vx[0], vx[1]), VY = pk(vy[0], vy[1]);
+                    const HaloX2 h2{dup(hc.invIc), dup(-hc.invR3), hc.R2};
+                    rk4_step_x2(X, Y, VX, VY,
+                                reinterpret_cast<const ulonglong2*>(s_coef + (size_t)n * 2 * C_COUNT),
+                                h2);
+                    x[0] = f2lo(X); x[1] = f2hi(X);
+                    y[0] = f2lo(Y); y[1] = f2hi(Y);
+                    vx[0] = f2lo(VX); vx[1] = f2hi(VX);
+                    vy[0] = f2lo(VY); vy[1] = f2hi(VY);
+                    continue;
+                }
                 T c[C_COUNT];
                 const float4* c4 = reinterpret_cast<const float4*>(s_coef + (size_t)n * C_COUNT);
 #pragma unroll
@@ -465,17 +617,19 @@ int launch_force_probe(int precision, const DevProblem* d_prob, int stage, const
     return NU_OK;
 }
 
-size_t coef_smem_bytes(int precision, int n_steps)
+size_t coef_smem_bytes(int precision, int n_steps, int tpt)
 {
-    return (size_t)n_steps * C_COUNT * (precision == NU_FP64 ? sizeof(double) : sizeof(float));
+    // the packed path stages the duplicated table (two floats per coefficient)
+    const size_t per = precision == NU_FP64 ? sizeof(double) : sizeof(float) * (tpt == 3 ? 2 : 1);
+    return (size_t)n_steps * C_COUNT * per;
 }
 
-template <typename T, int TPT, bool COUNT>
+template <typename T, int TPT, bool COUNT, bool PACKED = false>
 static int launch_t(int block, int grid, size_t smem, const DevProblem* d_probs, const int* d_prefix,
                     int n_probs, int n_tiles, unsigned* d_counter, unsigned long long* d_tallies,
                     cudaStream_t s)
 {
-    auto k = traj_kernel<T, TPT, COUNT>;
+    auto k = traj_kernel<T, TPT, COUNT, PACKED>;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
@@ -497,6 +651,7 @@ int launch_traj(int precision, int tpt, int block, int grid, size_t smem, const 
         if (tpt == 2) return launch_t<double, 2, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
         return launch_t<double, 1, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
     }
+    if (tpt == 3) return launch_t<float, 2, false, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
     if (tpt == 2) return launch_t<float, 2, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
     return launch_t<float, 1, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
 }
@@ -510,14 +665,14 @@ int launch_traj_tally(int precision, int tpt, int block, int grid, size_t smem,
         if (tpt == 2) return launch_t<double, 2, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
         return launch_t<double, 1, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
     }
-    if (tpt == 2) return launch_t<float, 2, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
+    if (tpt >= 2) return launch_t<float, 2, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
     return launch_t<float, 1, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
 }
 
-template <typename T, int TPT>
+template <typename T, int TPT, bool PACKED = false>
 static int occ_t(int block, size_t smem, int* out)
 {
-    auto k = traj_kernel<T, TPT, false>;
+    auto k = traj_kernel<T, TPT, false, PACKED>;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
@@ -531,6 +686,7 @@ static int occ_t(int block, size_t smem, int* out)
 int max_ctas_per_sm(int precision, int tpt, int block, size_t smem, int* out)
 {
     if (precision == NU_FP64) return tpt == 2 ? occ_t<double, 2>(block, smem, out) : occ_t<double, 1>(block, smem, out);
+    if (tpt == 3) return occ_t<float, 2, true>(block, smem, out);
     return tpt == 2 ? occ_t<float, 2>(block, smem, out) : occ_t<float, 1>(block, smem, out);
 }
 

@@ -84,9 +84,21 @@ def test_plan_rejects_invalid_inputs(bad):
     assert e.value.code in (nu.NU_EINVAL, nu.NU_ENOTSUP)
 
 
+def test_packed_shape_rules():
+    pb = W.plain_small(precision=W.MIXED)[0]
+    info = nu.plan(pb, block=256, tpt=3)            # two trajectories per thread, packed
+    assert info["tile"] == 512
+    with pytest.raises(nu.NuError) as e:
+        nu.plan(pb.replace(precision=W.FP64), block=256, tpt=3)
+    assert e.value.code == nu.NU_EINVAL
+    with pytest.raises(nu.NuError) as e:
+        nu.plan(pb.replace(n_steps=2000), block=256, tpt=3)
+    assert e.value.code == nu.NU_ENOTSUP
+
+
 def test_plan_rejects_bad_launch_shape_and_unsupported():
     pb = W.plain_small()[0]
-    for block, tpt in ((48, 1), (1024, 1), (100, 1), (256, 3)):
+    for block, tpt in ((48, 1), (1024, 1), (100, 1), (256, 4)):
         with pytest.raises(nu.NuError) as e:
             nu.plan(pb, block=block, tpt=tpt)
         assert e.value.code == nu.NU_EINVAL

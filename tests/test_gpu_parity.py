@@ -66,10 +66,12 @@ def test_random_small_all_kinds(seed):
                           conditioned_only=(pb.f_kind == W.F_FREEZEIN))
 
 
-@pytest.mark.parametrize("block,tpt", [(64, 1), (128, 2), (256, 1), (512, 2)])
+@pytest.mark.parametrize("block,tpt", [(64, 1), (128, 2), (256, 1), (512, 2), (128, 3), (256, 3)])
 @pytest.mark.parametrize("prec", [W.FP64, W.MIXED])
 def test_launch_shapes(block, tpt, prec):
     # ragged: 1000 trajectories per radius never fill the last tile
+    if tpt == 3 and prec != W.MIXED:
+        pytest.skip("the packed shape is a mixed-precision path")
     pb = W.plain_small(precision=prec)[0].replace(n_steps=200)
     got, _ = run_handle(pb, block=block, tpt=tpt)
     assert_parity(got, pb, where=f"block {block} tpt {tpt}")
@@ -163,3 +165,23 @@ def test_precision_sweep_full_size_sampled_radii():
         assert np.all(np.isfinite(g))
         e, _ = assert_parity(g, pb, sel=sel, where=f"m={pb.m_eV}", seeds=(1, 2, 3))
         assert np.all(e[1:] < TOL_MIXED)     # beyond the innermost kpc: stated tolerance
+
+
+@pytest.mark.parametrize("block", [128, 256, 512])
+def test_packed_path_is_bitwise_the_two_trajectory_path(block):
+    """The packed FP32x2 path performs the scalar two-trajectory path's
+    operations lane by lane: identical n/nbar, error estimate and q_i."""
+    cases = [W.plain_small(precision=W.MIXED)[0]] + W.random_small(6, n=4, precision=W.MIXED)
+    for pb in cases:
+        outs = []
+        for tpt in (2, 3):
+            h = nu.create(pb, block=block, tpt=tpt, flags=nu.NU_FLAG_KEEP_QI)
+            try:
+                nu.nu_profile_run(h)
+                r, e = nu.nu_profile_result(h, pb.n_radii)
+                q = nu.nu_profile_qi(h, pb.n_radii * pb.n_q * pb.n_mu)
+                outs.append((r, e, q))
+            finally:
+                nu.nu_profile_destroy(h)
+        for a, b in zip(outs[0], outs[1]):
+            assert np.array_equal(a, b)
