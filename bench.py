@@ -188,12 +188,14 @@ def bench_ours(args):
     # launch shape: autotuned (untimed) unless given as BLOCKxTPT
     if args.shape == "auto":
         tune = nu.nu_autotune(hs, stream)
-        block, tpt = tune["block"], tune["tpt"]
+        block, tpt, tflags = tune["block"], tune["tpt"], tune["flags"]
     else:
-        block, tpt = (int(v) for v in args.shape.lower().split("x"))
+        parts = args.shape.lower().split("x")
+        block, tpt = int(parts[0]), int(parts[1])
+        tflags = nu.NU_FLAG_GTAB if len(parts) > 2 and parts[2] == "g" else 0
         tune = None
     opts = nu.nu_opts()
-    opts.flags = nu.NU_FLAG_TIMING
+    opts.flags = nu.NU_FLAG_TIMING | tflags
     opts.stream = stream.cuda_stream
     opts.block, opts.tpt = block, tpt
     batch = nu.nu_batch_create(hs, opts)
@@ -281,7 +283,8 @@ def bench_ours(args):
     peak = fp32_peak_tflops(peak_mhz)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": f"traj_kernel<float,{tpt}>", "kernel_ms": kms,
+                "kernel": f"traj_kernel<float,{min(tpt, 2)},packed={tpt == 3},l1_table={bool(tflags)}>",
+                "kernel_ms": kms,
                 "flops_per_launch": flops, "flops_per_executed_traj_step": flops / live_steps,
                 "executed_traj_steps": live_steps,
                 "finished_early_frac": 1.0 - live_steps / traj_steps,
@@ -312,9 +315,11 @@ def bench_ours(args):
                        "precision": "mixed: FP32 state/force, FP64 tables and sums",
                        "l2": "flushed (256 MiB write) between timed steps",
                        "launch": f"one persistent batched launch per step: grid {grid} CTAs x {block} "
-                                 f"threads, {tpt} trajectories/thread",
+                                 f"threads, shape {block}x{tpt}{'xg' if tflags else ''} "
+                                 "(tpt 3 = two trajectories/thread in packed FP32x2; g = table via L1)",
                        "autotune": (None if tune is None else
-                                    {f"{b_}x{t_}": round(ms, 4) for b_, t_, ms in tune["candidates"]}),
+                                    {f"{b_}x{t_}{'xg' if f_ else ''}": round(ms, 4)
+                                     for b_, t_, f_, ms in tune["candidates"]}),
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": traj_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
@@ -335,7 +340,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--shape", default="auto",
-                    help="tile shape BLOCKxTPT (e.g. 256x1), or auto to run the autotuner first")
+                    help="launch shape BLOCKxTPT[xg] (e.g. 256x1, 256x3xg), or auto (autotuner)")
     ap.add_argument("--case", choices=("full", "small"), default="full",
                     help="small: one mass x 8 radii of the same workload, for profiler captures")
     args = ap.parse_args()

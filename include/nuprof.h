@@ -103,6 +103,10 @@ extern "C" {
 #define NU_FLAG_GRAPH    2 /* batches: capture the launch in a CUDA graph      */
 #define NU_FLAG_TIMING   4 /* batches: record CUDA events around the trajectory
                               kernel (read with nu_batch_kernel_ms)            */
+#define NU_FLAG_GTAB     8 /* batches: read the per-step coefficient table in
+                              place through the L1 cache instead of staging it
+                              in shared memory (frees shared memory, so more
+                              CTAs fit on an SM); results are identical        */
 
 typedef struct nu_cosmo {
     double Om;       /* matter density today; Omega_Lambda = 1 - Om (Sec. II.A) */
@@ -271,8 +275,9 @@ NU_API int nu_batch_kernel_ms(nu_batch* b, float* ms);
 NU_API int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts);
 
 /* Launch-shape autotuner: times the batch of requests `hs` with each candidate
- * tile shape (threads per CTA x trajectories per thread: 128x1, 256x1, 512x1,
- * 128x2, 256x2, and for mixed precision the packed 128x3, 256x3, 512x3; one
+ * launch shape (threads per CTA x trajectories per thread x table source:
+ * 256x1, 512x1, 256x2 staged in shared memory; 256x1, 384x1 through L1; and for
+ * mixed precision the packed 256x3 and 128x3 through L1 and 256x3 staged; one
  * warm-up and the median of three runs) and reports the
  * fastest.  With cache_path != NULL, a JSON-lines cache keyed by GPU name,
  * precision, step-count and trajectory-count buckets (powers of two) is read
@@ -282,11 +287,13 @@ NU_API int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts);
 typedef struct nu_tune_result {
     int block;               /* best threads per CTA                          */
     int tpt;                 /* best trajectories per thread                  */
+    int flags;               /* best table source (0 or NU_FLAG_GTAB)         */
     float best_ms;           /* trajectory-kernel time of one run with it     */
     int from_cache;          /* 1 if read from the cache (no timing done)     */
     int n_candidates;
     int cand_block[8];
     int cand_tpt[8];
+    int cand_flags[8];
     float cand_ms[8];
 } nu_tune_result;
 NU_API int nu_autotune(nu_profile* const* hs, int n, void* stream, const char* cache_path,

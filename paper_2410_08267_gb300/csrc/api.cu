@@ -83,10 +83,11 @@ int sm_count()
     return v;
 }
 
-int persistent_grid(int precision, int tpt, int block, size_t smem, int n_tiles, int* grid)
+int persistent_grid(int precision, int tpt, int block, size_t smem, int n_tiles, int* grid,
+                    bool gtab = false)
 {
     int per_sm = 0;
-    const int rc = max_ctas_per_sm(precision, tpt, block, smem, &per_sm);
+    const int rc = max_ctas_per_sm(precision, tpt, block, smem, &per_sm, gtab);
     if (rc != NU_OK) return rc;
     const int sms = sm_count();
     if (per_sm < 1 || sms < 1) return NU_ECUDA;
@@ -131,6 +132,7 @@ struct nu_batch {
     unsigned long long* d_tallies = nullptr;   // [5], allocated at the first count
     bool use_graph = false;
     bool timing = false;
+    bool gtab = false;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     bool timed_run = false;
     cudaGraphExec_t exec = nullptr;
@@ -532,6 +534,7 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
     resolve_opts(opts, o);
     if (opts) b->use_graph = (opts->flags & NU_FLAG_GRAPH) != 0;
     if (opts) b->timing = (opts->flags & NU_FLAG_TIMING) != 0;
+    if (opts) b->gtab = (opts->flags & NU_FLAG_GTAB) != 0;
     if (b->timing && (cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess)) {
         cudaGetLastError();
         return NU_ECUDA;
@@ -560,7 +563,7 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
     b->d_ctrl = reinterpret_cast<unsigned*>(base + o_ctrl);
     b->d_probs = reinterpret_cast<DevProblem*>(base + o_probs);
     b->d_prefix = reinterpret_cast<int*>(base + o_pref);
-    rc = persistent_grid(b->precision, b->tpt, b->block, b->smem, b->n_tiles, &b->grid);
+    rc = persistent_grid(b->precision, b->tpt, b->block, b->smem, b->n_tiles, &b->grid, b->gtab);
     if (rc != NU_OK) {
         b->mem.release();
         return rc;
@@ -575,7 +578,7 @@ static int batch_enqueue(nu_batch* b, cudaStream_t s, bool timed)
     if (cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return NU_ECUDA;
     if (timed && cudaEventRecord(b->t0, s) != cudaSuccess) return NU_ECUDA;
     const int rc = launch_traj(b->precision, b->tpt, b->block, b->grid, b->smem, b->d_probs,
-                               b->d_prefix, (int)b->hs.size(), b->n_tiles, b->d_ctrl, s);
+                               b->d_prefix, (int)b->hs.size(), b->n_tiles, b->d_ctrl, s, b->gtab);
     if (rc != NU_OK) return rc;
     if (timed && cudaEventRecord(b->t1, s) != cudaSuccess) return NU_ECUDA;
     return NU_OK;

@@ -24,9 +24,12 @@
 namespace {
 
 struct Shape {
-    int block, tpt;
+    int block, tpt, flags;
 };
-const Shape kShapes[] = {{128, 1}, {256, 1}, {512, 1}, {128, 2}, {256, 2}, {128, 3}, {256, 3}, {512, 3}};
+// threads per CTA, trajectories per thread (3: two, packed FP32x2), table source
+const Shape kShapes[] = {{256, 1, 0}, {512, 1, 0}, {256, 2, 0}, {256, 1, NU_FLAG_GTAB},
+                         {384, 1, NU_FLAG_GTAB}, {256, 3, NU_FLAG_GTAB}, {128, 3, NU_FLAG_GTAB},
+                         {256, 3, 0}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 int bucket_pow2(long long v)
@@ -71,12 +74,13 @@ bool cache_lookup(const char* path, const std::string& key, nu_tune_result* out)
     while (std::fgets(buf, sizeof(buf), f)) {
         std::string line(buf);
         if (line.compare(0, key.size(), key) != 0) continue;
-        int block = 0, tpt = 0;
+        int block = 0, tpt = 0, flags = 0;
         float ms = 0.0f;
         if (field_int(line, "block", &block) && field_int(line, "tpt", &tpt) &&
-            field_float(line, "ms", &ms)) {
+            field_int(line, "flags", &flags) && field_float(line, "ms", &ms)) {
             out->block = block;
             out->tpt = tpt;
+            out->flags = flags;
             out->best_ms = ms;
             found = true;
         }
@@ -89,8 +93,8 @@ void cache_store(const char* path, const std::string& key, const nu_tune_result&
 {
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s, \"block\": %d, \"tpt\": %d, \"ms\": %.6f}\n", key.c_str(), r.block, r.tpt,
-                 r.best_ms);
+    std::fprintf(f, "%s, \"block\": %d, \"tpt\": %d, \"flags\": %d, \"ms\": %.6f}\n", key.c_str(),
+                 r.block, r.tpt, r.flags, r.best_ms);
     std::fclose(f);
 }
 
@@ -131,7 +135,7 @@ extern "C" int nu_autotune(nu_profile* const* hs, int n, void* stream, const cha
         std::memset(&o, 0, sizeof(o));
         o.block = kShapes[c].block;
         o.tpt = kShapes[c].tpt;
-        o.flags = NU_FLAG_TIMING;
+        o.flags = NU_FLAG_TIMING | kShapes[c].flags;
         o.stream = stream;
         nu_batch* b = nullptr;
         int rc = nu_batch_create(hs, n, &o, &b);
@@ -147,12 +151,14 @@ extern "C" int nu_autotune(nu_profile* const* hs, int n, void* stream, const cha
         std::sort(t, t + 3);
         out->cand_block[slot] = o.block;
         out->cand_tpt[slot] = o.tpt;
+        out->cand_flags[slot] = kShapes[c].flags;
         out->cand_ms[slot] = t[1];
         ++slot;
         if (t[1] < best) {
             best = t[1];
             out->block = o.block;
             out->tpt = o.tpt;
+            out->flags = kShapes[c].flags;
             out->best_ms = t[1];
         }
     }

@@ -93,11 +93,12 @@ struct DevProblem {
 // Kernel launch helpers (traj_kernel.cu).
 int launch_traj(int precision, int tpt, int block, int grid, size_t smem_bytes,
                 const DevProblem* d_probs, const int* d_tile_prefix, int n_probs, int n_tiles,
-                unsigned* d_tile_counter, void* stream);
+                unsigned* d_tile_counter, void* stream, bool gtab = false);
 int launch_traj_tally(int precision, int tpt, int block, int grid, size_t smem_bytes,
                       const DevProblem* d_probs, const int* d_tile_prefix, int n_probs, int n_tiles,
                       unsigned* d_tile_counter, unsigned long long* d_tallies, void* stream);
-int max_ctas_per_sm(int precision, int tpt, int block, size_t smem_bytes, int* out);
+int max_ctas_per_sm(int precision, int tpt, int block, size_t smem_bytes, int* out,
+                    bool gtab = false);
 // Smallest tile (block 64 x 1 trajectory): request buffers of tile sums are
 // sized for it, so a batch may run any tile shape over existing requests.
 constexpr int kMinTile = 64;

@@ -354,9 +354,9 @@ __device__ __forceinline__ f2 accel_m_x2(f2 x, f2 y, f2 S, f2 Q, const HaloX2& h
     return pk(r2a < hc.R2 ? f2lo(m) : 0.0f, r2b < hc.R2 ? f2hi(m) : 0.0f);
 }
 
-// rk4_step for two trajectories at once; cq points at the step's 8 x 16 bytes
-// of the duplicated table (slot j -> floats 2j, 2j+1).
-__device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const ulonglong2* cq,
+// rk4_step for two trajectories at once; cq holds the step's 8 x 16 bytes of
+// the duplicated table (slot j -> floats 2j, 2j+1).
+__device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const ulonglong2 (&cq)[8],
                                             const HaloX2& hc)
 {
     const ulonglong2 q0 = cq[0], q1 = cq[1], q2 = cq[2], q3 = cq[3];
@@ -394,7 +394,7 @@ __device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const 
     y = ny;
 }
 
-template <typename T, int TPT, bool COUNT, bool PACKED = false>
+template <typename T, int TPT, bool COUNT, bool PACKED = false, bool GTAB = false>
 __global__ void __launch_bounds__(512)
 traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_prefix,
             int n_probs, int n_tiles, unsigned* __restrict__ tile_counter,
@@ -428,7 +428,10 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         const DevProblem& P = probs[lo];
         const int n_steps = P.n_steps;
 
-        if (lo != cur) {   // stage this request's coefficient table (uniform branch)
+        // coefficient table: staged once per request into shared memory, or
+        // (GTAB) read in place through the L1 cache with warp-uniform loads
+        const T* tab = GTAB ? reinterpret_cast<const T*>(PACKED ? P.coef2 : P.coef) : s_coef;
+        if (!GTAB && lo != cur) {   // stage this request's table (uniform branch)
             const float4* src = reinterpret_cast<const float4*>(PACKED ? P.coef2 : P.coef);
             float4* dst = reinterpret_cast<float4*>(s_coef);
             const int n16 = (int)((size_t)n_steps * C_COUNT * sizeof(T) * (PACKED ? 2 : 1) / 16);
@@ -488,9 +491,15 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                     f2 X = pk(x[0], x[1]), Y = pk(y[0], y[1]);
                     f2 VX = pk(vx[0], vx[1]), VY = pk(vy[0], vy[1]);
                     const HaloX2 h2{dup(hc.invIc), dup(-hc.invR3), hc.R2};
-                    rk4_step_x2(X, Y, VX, VY,
-                                reinterpret_cast<const ulonglong2*>(s_coef + (size_t)n * 2 * C_COUNT),
-                                h2);
+                    ulonglong2 cq[8];
+                    const uint4* src4 = reinterpret_cast<const uint4*>(tab + (size_t)n * 2 * C_COUNT);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const uint4 w = GTAB ? __ldg(&src4[q]) : src4[q];
+                        cq[q] = make_ulonglong2(((unsigned long long)w.y << 32) | w.x,
+                                                ((unsigned long long)w.w << 32) | w.z);
+                    }
+                    rk4_step_x2(X, Y, VX, VY, cq, h2);
                     x[0] = f2lo(X); x[1] = f2hi(X);
                     y[0] = f2lo(Y); y[1] = f2hi(Y);
                     vx[0] = f2lo(VX); vx[1] = f2hi(VX);
@@ -498,10 +507,10 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                     continue;
                 }
                 T c[C_COUNT];
-                const float4* c4 = reinterpret_cast<const float4*>(s_coef + (size_t)n * C_COUNT);
+                const float4* c4 = reinterpret_cast<const float4*>(tab + (size_t)n * C_COUNT);
 #pragma unroll
                 for (int q = 0; q < (int)(C_COUNT * sizeof(T) / 16); ++q)
-                    reinterpret_cast<float4*>(c)[q] = c4[q];
+                    reinterpret_cast<float4*>(c)[q] = GTAB ? __ldg(&c4[q]) : c4[q];
 #pragma unroll
                 for (int i = 0; i < TPT; ++i) {
                     ctr.set_live(!fin_i[i] && !done);
@@ -624,12 +633,13 @@ size_t coef_smem_bytes(int precision, int n_steps, int tpt)
     return (size_t)n_steps * C_COUNT * per;
 }
 
-template <typename T, int TPT, bool COUNT, bool PACKED = false>
+template <typename T, int TPT, bool COUNT, bool PACKED = false, bool GTAB = false>
 static int launch_t(int block, int grid, size_t smem, const DevProblem* d_probs, const int* d_prefix,
                     int n_probs, int n_tiles, unsigned* d_counter, unsigned long long* d_tallies,
                     cudaStream_t s)
 {
-    auto k = traj_kernel<T, TPT, COUNT, PACKED>;
+    auto k = traj_kernel<T, TPT, COUNT, PACKED, GTAB>;
+    if (GTAB) smem = 0;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
@@ -643,23 +653,34 @@ static int launch_t(int block, int grid, size_t smem, const DevProblem* d_probs,
     return NU_OK;
 }
 
+template <bool GTAB>
+static int launch_shape(int precision, int tpt, int block, int grid, size_t smem,
+                        const DevProblem* d_probs, const int* d_prefix, int n_probs, int n_tiles,
+                        unsigned* d_counter, cudaStream_t s)
+{
+    if (precision == NU_FP64) {
+        if (tpt == 2) return launch_t<double, 2, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+        return launch_t<double, 1, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+    }
+    if (tpt == 3) return launch_t<float, 2, false, true, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+    if (tpt == 2) return launch_t<float, 2, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+    return launch_t<float, 1, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+}
+
 int launch_traj(int precision, int tpt, int block, int grid, size_t smem, const DevProblem* d_probs,
-                const int* d_prefix, int n_probs, int n_tiles, unsigned* d_counter, void* stream)
+                const int* d_prefix, int n_probs, int n_tiles, unsigned* d_counter, void* stream,
+                bool gtab)
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (precision == NU_FP64) {
-        if (tpt == 2) return launch_t<double, 2, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
-        return launch_t<double, 1, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
-    }
-    if (tpt == 3) return launch_t<float, 2, false, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
-    if (tpt == 2) return launch_t<float, 2, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
-    return launch_t<float, 1, false>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+    if (gtab) return launch_shape<true>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
+    return launch_shape<false>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
 }
 
 int launch_traj_tally(int precision, int tpt, int block, int grid, size_t smem,
                       const DevProblem* d_probs, const int* d_prefix, int n_probs, int n_tiles,
                       unsigned* d_counter, unsigned long long* d_tallies, void* stream)
 {
+    // the tallies are trajectory facts: every shape integrates the same values
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (precision == NU_FP64) {
         if (tpt == 2) return launch_t<double, 2, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
@@ -669,10 +690,11 @@ int launch_traj_tally(int precision, int tpt, int block, int grid, size_t smem,
     return launch_t<float, 1, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
 }
 
-template <typename T, int TPT, bool PACKED = false>
+template <typename T, int TPT, bool PACKED = false, bool GTAB = false>
 static int occ_t(int block, size_t smem, int* out)
 {
-    auto k = traj_kernel<T, TPT, false, PACKED>;
+    auto k = traj_kernel<T, TPT, false, PACKED, GTAB>;
+    if (GTAB) smem = 0;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
@@ -683,11 +705,19 @@ static int occ_t(int block, size_t smem, int* out)
     return NU_OK;
 }
 
-int max_ctas_per_sm(int precision, int tpt, int block, size_t smem, int* out)
+template <bool GTAB>
+static int occ_shape(int precision, int tpt, int block, size_t smem, int* out)
 {
-    if (precision == NU_FP64) return tpt == 2 ? occ_t<double, 2>(block, smem, out) : occ_t<double, 1>(block, smem, out);
-    if (tpt == 3) return occ_t<float, 2, true>(block, smem, out);
-    return tpt == 2 ? occ_t<float, 2>(block, smem, out) : occ_t<float, 1>(block, smem, out);
+    if (precision == NU_FP64)
+        return tpt == 2 ? occ_t<double, 2, false, GTAB>(block, smem, out) : occ_t<double, 1, false, GTAB>(block, smem, out);
+    if (tpt == 3) return occ_t<float, 2, true, GTAB>(block, smem, out);
+    return tpt == 2 ? occ_t<float, 2, false, GTAB>(block, smem, out) : occ_t<float, 1, false, GTAB>(block, smem, out);
+}
+
+int max_ctas_per_sm(int precision, int tpt, int block, size_t smem, int* out, bool gtab)
+{
+    return gtab ? occ_shape<true>(precision, tpt, block, smem, out)
+                : occ_shape<false>(precision, tpt, block, smem, out);
 }
 
 }  // namespace nuprof

@@ -25,7 +25,7 @@ NU_ETOOBIG = -10
 NU_NOALLOC_MAX_BYTES = 4 << 20
 NU_FP64, NU_MIXED = 0, 1
 NU_RADII_KPC, NU_RADII_R200 = 0, 1
-NU_FLAG_KEEP_QI, NU_FLAG_GRAPH, NU_FLAG_TIMING = 1, 2, 4
+NU_FLAG_KEEP_QI, NU_FLAG_GRAPH, NU_FLAG_TIMING, NU_FLAG_GTAB = 1, 2, 4, 8
 NU_MAX_STEPS = 3000
 
 
@@ -81,9 +81,10 @@ class nu_peaks(C.Structure):
 
 
 class nu_tune_result(C.Structure):
-    _fields_ = [("block", C.c_int), ("tpt", C.c_int), ("best_ms", C.c_float),
+    _fields_ = [("block", C.c_int), ("tpt", C.c_int), ("flags", C.c_int), ("best_ms", C.c_float),
                 ("from_cache", C.c_int), ("n_candidates", C.c_int),
-                ("cand_block", C.c_int * 8), ("cand_tpt", C.c_int * 8), ("cand_ms", C.c_float * 8)]
+                ("cand_block", C.c_int * 8), ("cand_tpt", C.c_int * 8), ("cand_flags", C.c_int * 8),
+                ("cand_ms", C.c_float * 8)]
 
 
 _lib = None
@@ -332,8 +333,10 @@ def nu_autotune(handles: Sequence, stream=None, cache_path: Optional[str] = None
     r = nu_tune_result()
     _check(lib().nu_autotune(arr, len(handles), _stream_ptr(stream),
                              cache_path.encode() if cache_path else None, C.byref(r)), "nu_autotune")
-    return {"block": r.block, "tpt": r.tpt, "best_ms": r.best_ms, "from_cache": bool(r.from_cache),
-            "candidates": [(r.cand_block[i], r.cand_tpt[i], r.cand_ms[i]) for i in range(r.n_candidates)]}
+    return {"block": r.block, "tpt": r.tpt, "flags": r.flags, "best_ms": r.best_ms,
+            "from_cache": bool(r.from_cache),
+            "candidates": [(r.cand_block[i], r.cand_tpt[i], r.cand_flags[i], r.cand_ms[i])
+                           for i in range(r.n_candidates)]}
 
 
 def nu_batch_destroy(b):

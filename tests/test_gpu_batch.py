@@ -130,11 +130,32 @@ def test_autotune_picks_the_fastest_and_caches(tmp_path):
     try:
         cache = str(tmp_path / "tune.jsonl")
         r = nu.nu_autotune(hs, cache_path=cache)
-        assert not r["from_cache"] and len(r["candidates"]) == 6
-        assert r["best_ms"] == min(ms for _, _, ms in r["candidates"])
-        assert (r["block"], r["tpt"]) in [(b_, t_) for b_, t_, _ in r["candidates"]]
+        assert not r["from_cache"] and len(r["candidates"]) == 8
+        assert r["best_ms"] == min(ms for _, _, _, ms in r["candidates"])
+        assert (r["block"], r["tpt"], r["flags"]) in [(b_, t_, f_) for b_, t_, f_, _ in r["candidates"]]
         again = nu.nu_autotune(hs, cache_path=cache)
-        assert again["from_cache"] and (again["block"], again["tpt"]) == (r["block"], r["tpt"])
+        assert again["from_cache"] and (again["block"], again["tpt"], again["flags"]) == \
+            (r["block"], r["tpt"], r["flags"])
     finally:
         for h in hs:
             nu.nu_profile_destroy(h)
+
+
+def test_table_through_l1_is_bitwise_the_staged_table():
+    probs = [pb.replace(n_steps=150) for pb in W.batched_uneven(n_halos=5, seed=21)]
+    for tpt in (1, 2, 3):
+        outs = []
+        for flags in (0, nu.NU_FLAG_GTAB):
+            hs = [nu.create(pb) for pb in probs]
+            opts = nu.nu_opts()
+            opts.block, opts.tpt, opts.flags = 256, tpt, flags
+            b = nu.nu_batch_create(hs, opts)
+            try:
+                nu.nu_batch_run(b)
+                outs.append([nu.nu_profile_result(h, pb.n_radii)[0] for h, pb in zip(hs, probs)])
+            finally:
+                nu.nu_batch_destroy(b)
+                for h in hs:
+                    nu.nu_profile_destroy(h)
+        for a, c in zip(*outs):
+            assert np.array_equal(a, c)
