@@ -179,8 +179,8 @@ def bench_ours(args):
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     problems = W.precision_sweep(precision=W.MIXED)
-    if args.case == "small":            # profiling case: one mass, 8 radii
-        problems = [problems[SAMPLE_MASS_INDEX].replace(radii=np.geomspace(1.0, 1000.0, 8))]
+    if args.case == "small":            # profiling case: one mass, 24 radii (fills every SM)
+        problems = [problems[SAMPLE_MASS_INDEX].replace(radii=np.geomspace(1.0, 1000.0, 24))]
     traj_steps = sum(pb.traj_steps for pb in problems)
 
     with torch.cuda.stream(stream):
@@ -305,7 +305,7 @@ def bench_ours(args):
            "sample": f"m_nu=0.1 eV, radii {list(SAMPLE_RADII)} of 64, FP64, {dt:.1f} s wall"}
 
     if args.case == "small":
-        WORKLOAD_USED = "small profiling case of " + WORKLOAD + " (m_nu=0.1 eV, 8 radii)"
+        WORKLOAD_USED = "small profiling case of " + WORKLOAD + " (m_nu=0.1 eV, 24 radii)"
     else:
         WORKLOAD_USED = WORKLOAD
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -342,7 +342,7 @@ def main():
     ap.add_argument("--shape", default="auto",
                     help="launch shape BLOCKxTPT[xg] (e.g. 256x1, 256x3xg), or auto (autotuner)")
     ap.add_argument("--case", choices=("full", "small"), default="full",
-                    help="small: one mass x 8 radii of the same workload, for profiler captures")
+                    help="small: one mass x 24 radii of the same workload, for profiler captures")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
