@@ -394,8 +394,11 @@ __device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const 
     y = ny;
 }
 
+// The packed path asks for two 512-thread CTAs per SM (at most 64 registers):
+// it issues few instructions per trajectory, so it needs many warps to hide
+// the latency of its dependent chains.
 template <typename T, int TPT, bool COUNT, bool PACKED = false, bool GTAB = false>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, PACKED ? 2 : 1)
 traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_prefix,
             int n_probs, int n_tiles, unsigned* __restrict__ tile_counter,
             unsigned long long* __restrict__ tallies)
@@ -475,7 +478,33 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         // A warp stops integrating once all of its lanes are in that state
         // (padding lanes of a ragged tile start finished).  All lanes of the
         // warp reach the vote, so the full mask is valid.
-        {
+        if constexpr (PACKED) {
+            static_assert(TPT == 2, "packed path holds two trajectories");
+            f2 X = pk(x[0], x[1]), Y = pk(y[0], y[1]);
+            f2 VX = pk(vx[0], vx[1]), VY = pk(vy[0], vy[1]);
+            const HaloX2 h2{dup(hc.invIc), dup(-hc.invR3), hc.R2};
+            for (int n = 0; n < n_steps; ++n) {
+                const f2 r2 = fma2(X, X, mul2(Y, Y));
+                const f2 dot = fma2(X, VX, mul2(Y, VY));
+                const bool fin0 = !act[0] || (f2lo(r2) >= hc.R2 && f2lo(dot) <= 0.0f);
+                const bool fin1 = !act[1] || (f2hi(r2) >= hc.R2 && f2hi(dot) <= 0.0f);
+                done |= fin0 && fin1;
+                if (__all_sync(0xffffffffu, done)) break;
+                ulonglong2 cq[8];
+                const uint4* src4 = reinterpret_cast<const uint4*>(tab + (size_t)n * 2 * C_COUNT);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint4 w = GTAB ? __ldg(&src4[q]) : src4[q];
+                    cq[q] = make_ulonglong2(((unsigned long long)w.y << 32) | w.x,
+                                            ((unsigned long long)w.w << 32) | w.z);
+                }
+                rk4_step_x2(X, Y, VX, VY, cq, h2);
+            }
+            x[0] = f2lo(X); x[1] = f2hi(X);
+            y[0] = f2lo(Y); y[1] = f2hi(Y);
+            vx[0] = f2lo(VX); vx[1] = f2hi(VX);
+            vy[0] = f2lo(VY); vy[1] = f2hi(VY);
+        } else {
             for (int n = 0; n < n_steps; ++n) {
                 bool fin = true, fin_i[TPT];
 #pragma unroll
@@ -486,26 +515,6 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                 }
                 done |= fin;
                 if (__all_sync(0xffffffffu, done)) break;
-                if constexpr (PACKED) {
-                    static_assert(TPT == 2, "packed path holds two trajectories");
-                    f2 X = pk(x[0], x[1]), Y = pk(y[0], y[1]);
-                    f2 VX = pk(vx[0], vx[1]), VY = pk(vy[0], vy[1]);
-                    const HaloX2 h2{dup(hc.invIc), dup(-hc.invR3), hc.R2};
-                    ulonglong2 cq[8];
-                    const uint4* src4 = reinterpret_cast<const uint4*>(tab + (size_t)n * 2 * C_COUNT);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const uint4 w = GTAB ? __ldg(&src4[q]) : src4[q];
-                        cq[q] = make_ulonglong2(((unsigned long long)w.y << 32) | w.x,
-                                                ((unsigned long long)w.w << 32) | w.z);
-                    }
-                    rk4_step_x2(X, Y, VX, VY, cq, h2);
-                    x[0] = f2lo(X); x[1] = f2hi(X);
-                    y[0] = f2lo(Y); y[1] = f2hi(Y);
-                    vx[0] = f2lo(VX); vx[1] = f2hi(VX);
-                    vy[0] = f2lo(VY); vy[1] = f2hi(VY);
-                    continue;
-                }
                 T c[C_COUNT];
                 const float4* c4 = reinterpret_cast<const float4*>(tab + (size_t)n * C_COUNT);
 #pragma unroll
