@@ -161,6 +161,50 @@ def bench_reference(args):
     return 0
 
 
+def drive_stream(nu, srv, reqs, poll_sleep=2e-4, timeout_s=600.0):
+    """Submit each request at its arrival time and collect results; returns
+    (wall seconds from first arrival to last result, latencies ms, failures)."""
+    t0 = time.perf_counter()
+    outstanding = {}
+    lat, failed = [], 0
+    i = 0
+    while (i < len(reqs) or outstanding) and time.perf_counter() - t0 < timeout_s:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i].t_arrival <= now:
+            outstanding[nu.nu_server_submit(srv, reqs[i].problem)] = reqs[i].problem.n_radii
+            i += 1
+        for t in list(outstanding):
+            r = nu.nu_server_poll(srv, t, outstanding[t])
+            if r is None:
+                continue
+            del outstanding[t]
+            if r[0] == nu.NU_OK:
+                lat.append(r[3])
+            else:
+                failed += 1
+        time.sleep(poll_sleep)
+    return time.perf_counter() - t0, lat, failed + len(outstanding)
+
+
+def serve_once(nu, rate, n_requests, seed=2412, batched=True, chunk=100, budget=8 << 30):
+    """The serving workload (Poisson arrivals, mixed requests) through the
+    continuous-batching server, or through its one-request-per-launch form."""
+    reqs = W.serving_stream(rate=rate, n_requests=n_requests, seed=seed)
+    srv = (nu.nu_server_create(device_bytes=budget, chunk_steps=chunk, max_active=256) if batched
+           else nu.nu_server_create(device_bytes=budget, chunk_steps=0, max_active=1))
+    try:
+        wall, lat, failed = drive_stream(nu, srv, reqs)
+        st = nu.nu_server_stats(srv)
+    finally:
+        nu.nu_server_destroy(srv)
+    lat = np.asarray(lat)
+    return {"rate_per_s": rate, "requests": n_requests, "mode": "continuous" if batched else "one_per_launch",
+            "profiles_per_s": len(lat) / wall, "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None, "failed": failed,
+            "launches": st["iterations"], "max_active": st["max_active_seen"],
+            "traj_steps_per_s": st["traj_steps"] / wall, "gpu_busy_frac": st["busy_ms"] / 1e3 / wall}
+
+
 def bench_ours(args):
     import torch
 
@@ -250,6 +294,7 @@ def bench_ours(args):
             hh = [nu.create(pb, stream=stream) for pb in problems]
             o2 = nu.nu_opts()
             o2.stream = stream.cuda_stream
+            o2.block, o2.tpt, o2.flags = block, tpt, tflags     # the tuned launch shape
             b2 = nu.nu_batch_create(hh, o2)
             bh2d = nu.nu_batch_info(b2)["h2d_bytes"]
             nu.nu_batch_run(b2, stream)
@@ -267,6 +312,13 @@ def bench_ours(args):
     nu.nu_batch_destroy(batch)
     for h in hs:
         nu.nu_profile_destroy(h)
+
+    # ---- serving: the request stream, continuous batching vs one launch per request ----
+    serving = None
+    if args.serve_rate > 0 and args.case == "full":
+        n_req = args.serve_requests
+        serving = {"continuous": serve_once(nu, args.serve_rate, n_req, batched=True),
+                   "one_per_launch": serve_once(nu, args.serve_rate, n_req, batched=False)}
 
     if dist is not None:
         dist.barrier()
@@ -324,12 +376,26 @@ def bench_ours(args):
             "e2e": {"value": traj_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "path": "create (host tables -> device) + batch + run + result + destroy"},
-            "gpu_launches": launches, "wall_s": wall,
+            "gpu_launches": launches, "wall_s": wall, "serving": serving,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clock,
             "accuracy": {"max_rel_err_vs_oracle": float(rel.max()),
                          "per_radius": [float(x) for x in rel],
                          "sample": "m_nu=0.1 eV, radii 0,21,42,63"}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_serve_sweep(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2410_08267_gb300 import nuprof as nu
+    for rate in (10, 30, 100, 300, 1000, 3000, 5000):
+        n_req = int(min(args.serve_requests, max(20, rate * 2)))
+        for batched in (True, False):
+            r = serve_once(nu, rate, n_req, batched=batched)
+            print(json.dumps({"metric": "served profiles/s", **r}), flush=True)
     return 0
 
 
@@ -343,7 +409,14 @@ def main():
                     help="launch shape BLOCKxTPT[xg] (e.g. 256x1, 256x3xg), or auto (autotuner)")
     ap.add_argument("--case", choices=("full", "small"), default="full",
                     help="small: one mass x 24 radii of the same workload, for profiler captures")
+    ap.add_argument("--serve-rate", type=float, default=300.0,
+                    help="request rate of the serving leg (0: skip it)")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="only the serving workload at rates 10..5000 /s, one JSON line per rate and mode")
     args = ap.parse_args()
+    if args.serve_sweep:
+        return bench_serve_sweep(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -305,6 +305,65 @@ NU_API int nu_autotune(nu_profile* const* hs, int n, void* stream, const char* c
 NU_API int nu_batch_info(const nu_batch* b, int* n_tiles, long long* traj_steps,
                          long long* h2d_bytes, int* grid);
 
+/* ---- continuous-batching request server ------------------------------------
+ * For rapid scans (the use the paper names: many cosmologies, halo and relic
+ * masses and grids), requests are queued and served together: a worker thread
+ * admits queued requests first come, first served while a device budget (one
+ * arena, sub-allocated first fit) and a slot limit allow, and runs one
+ * persistent trajectory launch per iteration over every admitted request,
+ * advancing each by chunk_steps RK4 steps with its trajectories' state kept
+ * on the device.  Requests arriving meanwhile join at the next launch; a
+ * request that reaches its last step forms its quadrature (Eq. localdensity)
+ * in that launch and leaves, freeing memory.  A request's result is bitwise
+ * the one nu_profile_run gives it alone with the same tile shape.  Every wait
+ * on the GPU is bounded by gpu_timeout_ms. */
+typedef struct nu_server nu_server;
+typedef struct nu_server_opts {
+    size_t device_bytes;     /* device memory budget of the server (>= 1 MiB)     */
+    int max_active;          /* requests on the GPU at once (0 -> 1024)           */
+    int chunk_steps;         /* RK4 steps per launch (0: a request's whole run)   */
+    int precision;           /* NU_FP64 or NU_MIXED: every request uses it        */
+    int block, tpt, flags;   /* launch shape (0: 128 x 3 with NU_FLAG_GTAB for mixed,
+                                256 x 1 for FP64)                                 */
+    nu_alloc_fn alloc;       /* where the budget comes from (NULL: cudaMalloc)    */
+    nu_free_fn free;
+    void* alloc_ctx;
+    double gpu_timeout_ms;   /* bound on one launch (<= 0 -> 60000)               */
+} nu_server_opts;
+
+typedef struct nu_serve_stats {
+    long long submitted, admitted, completed, cancelled, rejected;
+    long long iterations;    /* launches                                          */
+    long long traj_steps;    /* trajectory-steps advanced                          */
+    double busy_ms;          /* host-measured time of the launches                 */
+    double p50_ms, p99_ms, mean_ms;   /* submit -> result latency of completed ones */
+    int pending, active, max_active_seen;
+    int status;              /* NU_OK, or the error that stopped the server        */
+    long long arena_bytes, arena_peak;
+} nu_serve_stats;
+
+/* Start a server on the current device.  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
+NU_API int nu_server_create(const nu_server_opts* opts, nu_server** out);
+/* Queue a request (arguments as for nu_profile_create; opts may be NULL and
+ * only its n_steps, z_end and radii_unit are used).  Returns a ticket at once;
+ * the request is validated first (NU_EINVAL / NU_ENOTSUP), and a request that
+ * can never fit the budget later completes with NU_ENOMEM. */
+NU_API int nu_server_submit(nu_server* s, const nu_cosmo* cosmo, const nu_halo* halo,
+                            const nu_relic* relic, const double* radii, int n_radii,
+                            const nu_pgrid* p_grid, const nu_opts* opts, long long* ticket);
+/* NU_EAGAIN while the request runs; when it is done, copies n/nbar, the error
+ * estimate (may be NULL) and the submit-to-result latency (may be NULL) and
+ * returns the request's status (NU_OK, NU_ECANCELED, NU_ENOMEM, NU_ETIMEDOUT ...)
+ * once; NU_EINVAL for an unknown or already delivered ticket or a wrong n_radii. */
+NU_API int nu_server_poll(nu_server* s, long long ticket, double* n_over_nbar, double* err_est,
+                          int n_radii, double* latency_ms);
+/* Cancel a queued or running request (it completes with NU_ECANCELED before
+ * its next launch).  NU_EINVAL if the ticket is unknown or already done. */
+NU_API int nu_server_cancel(nu_server* s, long long ticket);
+NU_API int nu_server_stats(nu_server* s, nu_serve_stats* out);
+/* Stop the worker (after the launch in flight) and release everything. */
+NU_API void nu_server_destroy(nu_server* s);
+
 /* Maximum device scratch of nu_profile_compute_noalloc (a static array). */
 #define NU_NOALLOC_MAX_BYTES (4u << 20)
 

@@ -187,6 +187,32 @@ void put(std::vector<unsigned char>& buf, size_t off, const double* v, size_t n)
 
 }  // namespace
 
+namespace nuprof {
+
+const DevProblem& profile_desc(const nu_profile* h) { return h->hdp; }
+int profile_n_radii(const nu_profile* h) { return h->n_radii; }
+int profile_n_steps(const nu_profile* h) { return h->opts.n_steps; }
+long long profile_n_traj(const nu_profile* h) { return h->info.n_traj; }
+
+// Copy n/nbar and the error estimate of the last completed launch touching
+// the handle (ordered on `stream`); the caller guarantees that launch is done.
+int profile_read(const nu_profile* h, double* out, double* err, void* stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)h->n_radii * sizeof(double);
+    if (cudaMemcpyAsync(out, h->hdp.out, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        (err && cudaMemcpyAsync(err, h->hdp.err, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    for (int i = 0; i < h->n_radii; ++i)
+        if (!std::isfinite(out[i])) return NU_EDEVICE;
+    return NU_OK;
+}
+
+}  // namespace nuprof
+
 extern "C" {
 
 int nu_version(void) { return NU_VERSION_MAJOR * 10000 + NU_VERSION_MINOR * 100 + NU_VERSION_PATCH; }

@@ -88,7 +88,21 @@ struct DevProblem {
     int n_radii, n_q, n_mu, n_steps;
     int tiles_per_seg, tile;
     int precision;
+    // Chunked integration (serving): when `state` is set, a launch advances
+    // steps [step_begin, step_end) and keeps each trajectory's (x, y, vx, vy)
+    // in `state` ([n_radii][n_q][n_mu] of 4 values in the state precision);
+    // only the launch that reaches n_steps forms the quadrature.  step_end = 0
+    // means n_steps (a whole run).
+    void* state;
+    int step_begin, step_end;
 };
+
+// Accessors used by the request server (api.cu).
+const DevProblem& profile_desc(const nu_profile* h);
+int profile_n_radii(const nu_profile* h);
+int profile_n_steps(const nu_profile* h);
+long long profile_n_traj(const nu_profile* h);
+int profile_read(const nu_profile* h, double* out, double* err, void* stream);
 
 // Kernel launch helpers (traj_kernel.cu).
 int launch_traj(int precision, int tpt, int block, int grid, size_t smem_bytes,

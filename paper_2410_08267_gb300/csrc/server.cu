@@ -1,0 +1,588 @@
+// Continuous-batching request server for overdensity profiles.
+//
+// Rapid scanning (many cosmologies, halo masses, relic masses and grids) means
+// a stream of requests of very different sizes.  The server keeps the GPU busy
+// with all of them at once: a worker thread admits queued requests first come,
+// first served while the device budget (one arena, sub-allocated first fit)
+// and the slot limit allow, and runs one persistent trajectory launch per
+// iteration over every admitted request.  Each launch advances every request
+// by a chunk of RK4 steps, with the trajectories' state kept in device memory
+// between launches; a request that reaches its last step forms its quadrature
+// in that launch and leaves, freeing its memory for the next ones.  Requests
+// that arrive while others are on the GPU therefore join at the next launch
+// and share it (iteration-level batching).  Because a request is integrated
+// with the same operations and the same tiles whatever shares its launches,
+// its result is bitwise the one it gets alone.
+//
+// Every wait on the GPU is bounded (gpu_timeout_ms): a launch that does not
+// complete in time fails the requests it carried with NU_ETIMEDOUT and the
+// server stops admitting work.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <set>
+#include <thread>
+#include <vector>
+
+#include "nuprof_internal.h"
+
+using namespace nuprof;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point t0) { return std::chrono::duration<double, std::milli>(Clock::now() - t0).count(); }
+
+size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// First-fit sub-allocator over one device block (offsets, 256-byte aligned).
+class Arena {
+public:
+    void reset(void* base, size_t bytes)
+    {
+        base_ = static_cast<unsigned char*>(base);
+        size_ = bytes;
+        free_.clear();
+        free_[0] = bytes;
+        used_ = peak_ = 0;
+    }
+    void* alloc(size_t bytes)
+    {
+        bytes = up256(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            const size_t off = it->first, len = it->second;
+            free_.erase(it);
+            if (len > bytes) free_[off + bytes] = len - bytes;
+            sizes_[off] = bytes;
+            used_ += bytes;
+            peak_ = std::max(peak_, used_);
+            return base_ + off;
+        }
+        return nullptr;
+    }
+    void release(void* p)
+    {
+        if (!p) return;
+        const size_t off = static_cast<unsigned char*>(p) - base_;
+        auto s = sizes_.find(off);
+        if (s == sizes_.end()) return;
+        size_t len = s->second;
+        sizes_.erase(s);
+        used_ -= len;
+        size_t start = off;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && next->first == off + len) {   // merge right
+            len += next->second;
+            free_.erase(next);
+        }
+        auto prev = free_.lower_bound(off);
+        if (prev != free_.begin()) {                                // merge left
+            --prev;
+            if (prev->first + prev->second == off) {
+                start = prev->first;
+                len += prev->second;
+                free_.erase(prev);
+            }
+        }
+        free_[start] = len;
+    }
+    size_t size() const { return size_; }
+    size_t used() const { return used_; }
+    size_t peak() const { return peak_; }
+
+private:
+    unsigned char* base_ = nullptr;
+    size_t size_ = 0, used_ = 0, peak_ = 0;
+    std::map<size_t, size_t> free_;    // offset -> length
+    std::map<size_t, size_t> sizes_;   // offset -> length of live blocks
+};
+
+void* arena_alloc_cb(size_t bytes, void* ctx) { return static_cast<Arena*>(ctx)->alloc(bytes); }
+void arena_free_cb(void* p, size_t, void* ctx) { static_cast<Arena*>(ctx)->release(p); }
+
+struct Pending {
+    long long ticket;
+    nu_cosmo cosmo;
+    nu_halo halo;
+    nu_relic relic;
+    nu_pgrid grid;
+    nu_opts opts;
+    std::vector<double> radii;
+    Clock::time_point t_submit;
+};
+
+struct Active {
+    long long ticket;
+    nu_profile* h;
+    void* state;
+    int progress;
+    int n_steps;
+    bool cancelled;
+    Clock::time_point t_submit;
+};
+
+struct Done {
+    int rc;
+    std::vector<double> out, err;
+    double latency_ms;
+};
+
+}  // namespace
+
+struct nu_server {
+    nu_server_opts o;
+    int device = 0;
+    void* block = nullptr;                  // the arena's device memory
+    Arena arena;
+    cudaStream_t compute = nullptr, upload = nullptr;
+    cudaEvent_t ev = nullptr;
+    DevProblem* d_desc[2] = {nullptr, nullptr};   // per-iteration descriptors (double buffer)
+    int* d_prefix[2] = {nullptr, nullptr};
+    unsigned* d_ctrl = nullptr;
+    size_t capacity = 0;                    // arena bytes left for requests
+
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Pending> pending;
+    std::map<long long, Done> done;
+    std::set<long long> delivered;
+    std::map<long long, bool> cancel_requests;
+    std::vector<Active> active;
+    long long next_ticket = 1;
+    bool stop = false;
+    int fatal = NU_OK;
+    std::thread worker;
+
+    // statistics (under mu)
+    long long submitted = 0, admitted = 0, completed = 0, cancelled = 0, rejected = 0;
+    long long iterations = 0, traj_steps = 0;
+    double busy_ms = 0.0;
+    int max_active_seen = 0;
+    std::vector<double> latencies;
+
+    void run();
+    void finish(Active& a, int rc, std::vector<double>* out, std::vector<double>* err);
+};
+
+void nu_server::finish(Active& a, int rc, std::vector<double>* out, std::vector<double>* err)
+{
+    Done d;
+    d.rc = rc;
+    if (out) d.out.swap(*out);
+    if (err) d.err.swap(*err);
+    d.latency_ms = ms_since(a.t_submit);
+    nu_profile_destroy(a.h);                 // returns its memory to the arena
+    arena.release(a.state);
+    std::lock_guard<std::mutex> g(mu);
+    if (rc == NU_OK) {
+        ++completed;
+        latencies.push_back(d.latency_ms);
+    } else if (rc == NU_ECANCELED) {
+        ++cancelled;
+    }
+    done[a.ticket] = std::move(d);
+}
+
+void nu_server::run()
+{
+    cudaSetDevice(device);
+    const int tpt = o.tpt;
+    const int tile = o.block * traj_per_thread(tpt);
+    const bool gtab = (o.flags & NU_FLAG_GTAB) != 0;
+    int slot = 0;
+    for (;;) {
+        // ---- admission: first come, first served, while memory and slots allow ----
+        for (;;) {
+            Pending p;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                if (stop) return;
+                if (active.empty() && pending.empty())
+                    cv.wait_for(lk, std::chrono::milliseconds(20));
+                if (stop) return;
+                if (pending.empty() || (int)active.size() >= o.max_active || fatal != NU_OK) break;
+                auto c = cancel_requests.find(pending.front().ticket);
+                if (c != cancel_requests.end()) {
+                    Done d{NU_ECANCELED, {}, {}, ms_since(pending.front().t_submit)};
+                    done[pending.front().ticket] = d;
+                    ++cancelled;
+                    cancel_requests.erase(c);
+                    pending.pop_front();
+                    continue;
+                }
+                p = pending.front();
+            }
+            nu_plan_info info;
+            int rc = nu_profile_plan(&p.cosmo, &p.halo, &p.relic, p.radii.data(), (int)p.radii.size(),
+                                     &p.grid, &p.opts, &info);
+            const size_t sz = o.precision == NU_FP64 ? sizeof(double) : sizeof(float);
+            const size_t state_bytes = (size_t)info.n_traj * 4 * sz;
+            if (rc == NU_OK && up256((size_t)info.device_bytes) + up256(state_bytes) > capacity)
+                rc = NU_ENOMEM;                       // can never fit: refuse
+            nu_profile* h = nullptr;
+            void* state = nullptr;
+            if (rc == NU_OK) {
+                state = arena.alloc(state_bytes);
+                if (state) rc = nu_profile_create(&p.cosmo, &p.halo, &p.relic, p.radii.data(),
+                                                  (int)p.radii.size(), &p.grid, &p.opts, &h);
+                if (!state || rc == NU_ENOMEM) {
+                    arena.release(state);
+                    if (h) nu_profile_destroy(h);
+                    if (!active.empty()) break;       // no room now: wait for requests to leave
+                    rc = NU_ENOMEM;                   // nothing to wait for: refuse
+                    state = nullptr;
+                    h = nullptr;
+                }
+            }
+            std::lock_guard<std::mutex> g(mu);
+            pending.pop_front();
+            if (rc != NU_OK) {
+                arena.release(state);
+                done[p.ticket] = Done{rc, {}, {}, ms_since(p.t_submit)};
+                ++rejected;
+                continue;
+            }
+            active.push_back(Active{p.ticket, h, state, 0, profile_n_steps(h), false, p.t_submit});
+            ++admitted;
+            max_active_seen = std::max(max_active_seen, (int)active.size());
+        }
+        {
+            std::lock_guard<std::mutex> g(mu);
+            for (auto& a : active) {
+                auto c = cancel_requests.find(a.ticket);
+                if (c != cancel_requests.end()) {
+                    a.cancelled = true;
+                    cancel_requests.erase(c);
+                }
+            }
+        }
+        // retire cancelled requests before the launch
+        for (size_t i = 0; i < active.size();) {
+            if (active[i].cancelled) {
+                finish(active[i], NU_ECANCELED, nullptr, nullptr);
+                active.erase(active.begin() + i);
+            } else {
+                ++i;
+            }
+        }
+        if (active.empty()) continue;
+
+        // ---- one launch: every active request advances by one chunk ----
+        std::vector<DevProblem> desc(active.size());
+        std::vector<int> prefix(active.size() + 1, 0);
+        long long steps_this = 0;
+        size_t smem = 0;                          // the largest table staged this launch
+        for (size_t i = 0; i < active.size(); ++i) {
+            const Active& a = active[i];
+            smem = std::max(smem, coef_smem_bytes(o.precision, a.n_steps, tpt));
+            DevProblem d = profile_desc(a.h);
+            const long long seg = (long long)d.n_q * d.n_mu;
+            d.tile = tile;
+            d.tiles_per_seg = (int)((seg + tile - 1) / tile);
+            d.state = a.state;
+            d.step_begin = a.progress;
+            d.step_end = std::min(a.n_steps, a.progress + (o.chunk_steps > 0 ? o.chunk_steps : a.n_steps));
+            desc[i] = d;
+            prefix[i + 1] = prefix[i] + d.tiles_per_seg * d.n_radii;
+            steps_this += profile_n_traj(a.h) * (d.step_end - d.step_begin);
+        }
+        const int n = (int)active.size();
+        int rc = NU_OK;
+        if (cudaMemcpyAsync(d_desc[slot], desc.data(), n * sizeof(DevProblem), cudaMemcpyHostToDevice,
+                            compute) != cudaSuccess ||
+            cudaMemcpyAsync(d_prefix[slot], prefix.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                            compute) != cudaSuccess ||
+            cudaMemsetAsync(d_ctrl, 0, 2 * sizeof(unsigned), compute) != cudaSuccess)
+            rc = NU_ECUDA;
+        int grid = 0, per_sm = 0, sms = 0;
+        if (rc == NU_OK) rc = max_ctas_per_sm(o.precision, tpt, o.block, smem, &per_sm, gtab);
+        if (rc == NU_OK && (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+                            per_sm < 1))
+            rc = NU_ECUDA;
+        if (rc == NU_OK) {
+            grid = std::max(1, std::min(prefix[n], per_sm * sms));
+            rc = launch_traj(o.precision, tpt, o.block, grid, smem, d_desc[slot], d_prefix[slot], n,
+                             prefix[n], d_ctrl, compute, gtab);
+        }
+        const auto t_launch = Clock::now();
+        if (rc == NU_OK && cudaEventRecord(ev, compute) != cudaSuccess) rc = NU_ECUDA;
+        // bounded wait for the launch (requests keep arriving meanwhile)
+        while (rc == NU_OK) {
+            const cudaError_t q = cudaEventQuery(ev);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) {
+                rc = NU_ECUDA;
+                break;
+            }
+            if (ms_since(t_launch) > o.gpu_timeout_ms) {
+                rc = NU_ETIMEDOUT;
+                break;
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        const double launch_ms = ms_since(t_launch);
+        slot ^= 1;
+        if (rc != NU_OK) {
+            cudaGetLastError();
+            {
+                std::lock_guard<std::mutex> g(mu);
+                fatal = rc;
+            }
+            if (rc == NU_ETIMEDOUT) {
+                // the GPU may still be running the launch: fail the requests but
+                // keep their memory (it may still be written)
+                std::lock_guard<std::mutex> g(mu);
+                for (auto& a : active) done[a.ticket] = Done{rc, {}, {}, ms_since(a.t_submit)};
+                active.clear();
+                return;
+            }
+            for (auto& a : active) finish(a, rc, nullptr, nullptr);
+            active.clear();
+            continue;
+        }
+        {
+            std::lock_guard<std::mutex> g(mu);
+            ++iterations;
+            traj_steps += steps_this;
+            busy_ms += launch_ms;
+        }
+        // ---- retire the requests that reached their last step ----
+        for (size_t i = 0; i < active.size();) {
+            Active& a = active[i];
+            a.progress = desc[i].step_end;
+            if (a.progress < a.n_steps) {
+                ++i;
+                continue;
+            }
+            const int nr = profile_n_radii(a.h);
+            std::vector<double> out(nr), err(nr);
+            const int r = profile_read(a.h, out.data(), err.data(), upload);
+            finish(a, r, &out, &err);
+            active.erase(active.begin() + i);
+        }
+    }
+}
+
+extern "C" {
+
+int nu_server_create(const nu_server_opts* opts, nu_server** out)
+{
+    if (!opts || !out) return NU_EINVAL;
+    std::unique_ptr<nu_server> s(new (std::nothrow) nu_server());
+    if (!s) return NU_ENOMEM;
+    s->o = *opts;
+    nu_server_opts& o = s->o;
+    if (o.precision != NU_FP64 && o.precision != NU_MIXED) return NU_EINVAL;
+    if (o.max_active <= 0) o.max_active = 1024;
+    if (o.max_active > 65536) return NU_EINVAL;
+    if (o.block == 0) o.block = o.precision == NU_MIXED ? 128 : 256;
+    if (o.tpt == 0) {
+        o.tpt = o.precision == NU_MIXED ? kTptPacked : 1;
+        if (o.precision == NU_MIXED && o.flags == 0) o.flags = NU_FLAG_GTAB;
+    }
+    if (o.block < 64 || o.block > 512 || o.block % 32 != 0) return NU_EINVAL;
+    if (o.tpt != 1 && o.tpt != 2 && o.tpt != kTptPacked) return NU_EINVAL;
+    if (o.tpt == kTptPacked && o.precision != NU_MIXED) return NU_EINVAL;
+    if (o.chunk_steps < 0) return NU_EINVAL;
+    if (o.gpu_timeout_ms <= 0.0) o.gpu_timeout_ms = 60000.0;
+    if (o.device_bytes < ((size_t)1 << 20)) return NU_EINVAL;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    if (o.alloc) {
+        s->block = o.alloc(o.device_bytes, o.alloc_ctx);
+        if (!s->block) return NU_ENOMEM;
+    } else if (cudaMalloc(&s->block, o.device_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ENOMEM;
+    }
+    s->arena.reset(s->block, o.device_bytes);
+    for (int i = 0; i < 2; ++i) {
+        s->d_desc[i] = static_cast<DevProblem*>(s->arena.alloc((size_t)o.max_active * sizeof(DevProblem)));
+        s->d_prefix[i] = static_cast<int*>(s->arena.alloc((size_t)(o.max_active + 1) * sizeof(int)));
+    }
+    s->d_ctrl = static_cast<unsigned*>(s->arena.alloc(256));
+    s->capacity = s->arena.size() - s->arena.used();
+    auto fail = [&](int rc) {
+        if (s->compute) cudaStreamDestroy(s->compute);
+        if (s->upload) cudaStreamDestroy(s->upload);
+        if (s->ev) cudaEventDestroy(s->ev);
+        if (o.alloc) {
+            if (o.free) o.free(s->block, o.device_bytes, o.alloc_ctx);
+        } else {
+            cudaFree(s->block);
+        }
+        return rc;
+    };
+    if (!s->d_desc[0] || !s->d_desc[1] || !s->d_prefix[0] || !s->d_prefix[1] || !s->d_ctrl)
+        return fail(NU_ENOMEM);
+    if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NU_ECUDA);
+    }
+    nu_server* raw = s.get();
+    raw->worker = std::thread([raw] { raw->run(); });
+    *out = s.release();
+    return NU_OK;
+}
+
+int nu_server_submit(nu_server* s, const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
+                     const double* radii, int n_radii, const nu_pgrid* p_grid, const nu_opts* opts,
+                     long long* ticket)
+{
+    if (!s || !cosmo || !halo || !relic || !radii || n_radii < 1 || !p_grid || !ticket) return NU_EINVAL;
+    Pending p;
+    p.cosmo = *cosmo;
+    p.halo = *halo;
+    p.relic = *relic;
+    p.grid = *p_grid;
+    std::memset(&p.opts, 0, sizeof(p.opts));
+    if (opts) {
+        p.opts.n_steps = opts->n_steps;
+        p.opts.z_end = opts->z_end;
+        p.opts.radii_unit = opts->radii_unit;
+    }
+    p.opts.precision = s->o.precision;
+    p.opts.block = s->o.block;
+    p.opts.tpt = s->o.tpt;
+    p.opts.alloc = arena_alloc_cb;
+    p.opts.free = arena_free_cb;
+    p.opts.alloc_ctx = &s->arena;
+    p.opts.stream = s->upload;
+    p.radii.assign(radii, radii + n_radii);
+    nu_plan_info info;
+    const int rc = nu_profile_plan(&p.cosmo, &p.halo, &p.relic, radii, n_radii, &p.grid, &p.opts, &info);
+    if (rc != NU_OK) return rc;
+    p.t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (s->fatal != NU_OK) return s->fatal;
+        p.ticket = s->next_ticket++;
+        *ticket = p.ticket;
+        s->pending.push_back(std::move(p));
+        ++s->submitted;
+    }
+    s->cv.notify_one();
+    return NU_OK;
+}
+
+int nu_server_poll(nu_server* s, long long ticket, double* n_over_nbar, double* err_est, int n_radii,
+                   double* latency_ms)
+{
+    if (!s || !n_over_nbar) return NU_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->done.find(ticket);
+    if (it == s->done.end()) {
+        if (ticket < 1 || ticket >= s->next_ticket || s->delivered.count(ticket)) return NU_EINVAL;
+        return NU_EAGAIN;
+    }
+    const Done& d = it->second;
+    if (latency_ms) *latency_ms = d.latency_ms;
+    const int rc = d.rc;
+    if (rc == NU_OK) {
+        if ((int)d.out.size() != n_radii) return NU_EINVAL;
+        std::memcpy(n_over_nbar, d.out.data(), n_radii * sizeof(double));
+        if (err_est) std::memcpy(err_est, d.err.data(), n_radii * sizeof(double));
+    }
+    s->done.erase(it);
+    s->delivered.insert(ticket);
+    return rc;
+}
+
+int nu_server_cancel(nu_server* s, long long ticket)
+{
+    if (!s) return NU_EINVAL;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (ticket < 1 || ticket >= s->next_ticket) return NU_EINVAL;
+        if (s->done.count(ticket)) return NU_EINVAL;      // already finished
+        s->cancel_requests[ticket] = true;
+    }
+    s->cv.notify_one();
+    return NU_OK;
+}
+
+int nu_server_stats(nu_server* s, nu_serve_stats* out)
+{
+    if (!s || !out) return NU_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = s->submitted;
+    out->admitted = s->admitted;
+    out->completed = s->completed;
+    out->cancelled = s->cancelled;
+    out->rejected = s->rejected;
+    out->iterations = s->iterations;
+    out->traj_steps = s->traj_steps;
+    out->busy_ms = s->busy_ms;
+    out->pending = (int)s->pending.size();
+    out->active = (int)s->active.size();
+    out->max_active_seen = s->max_active_seen;
+    out->arena_bytes = (long long)s->arena.size();
+    out->arena_peak = (long long)s->arena.peak();
+    out->status = s->fatal;
+    if (!s->latencies.empty()) {
+        std::vector<double> l = s->latencies;
+        std::sort(l.begin(), l.end());
+        auto pct = [&](double p) {
+            const double pos = p * (l.size() - 1);
+            const size_t i = (size_t)pos;
+            const double f = pos - i;
+            return i + 1 < l.size() ? l[i] * (1 - f) + l[i + 1] * f : l[i];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        double m = 0;
+        for (double v : l) m += v;
+        out->mean_ms = m / l.size();
+    }
+    return NU_OK;
+}
+
+void nu_server_destroy(nu_server* s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaSetDevice(s->device);
+    const bool gpu_ok = s->fatal != NU_ETIMEDOUT;
+    if (gpu_ok) {
+        cudaStreamSynchronize(s->compute);
+        for (auto& a : s->active) {
+            nu_profile_destroy(a.h);
+            s->arena.release(a.state);
+        }
+    }
+    // after a timeout the arena may still be in use by the GPU: it is leaked
+    // rather than freed under a running kernel
+    if (gpu_ok) {
+        if (s->o.alloc) {
+            if (s->o.free) s->o.free(s->block, s->o.device_bytes, s->o.alloc_ctx);
+        } else {
+            cudaFree(s->block);
+        }
+    }
+    cudaStreamDestroy(s->compute);
+    cudaStreamDestroy(s->upload);
+    cudaEventDestroy(s->ev);
+    delete s;
+}
+
+}  // extern "C"

@@ -452,6 +452,11 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         const typename PrecTraits<T>::Halo hc = PrecTraits<T>::halo(P);
         const T x0 = reinterpret_cast<const T*>(P.x0)[seg];
 
+        // steps of this launch: all of them, or one chunk of a served request
+        const int s_begin = P.step_begin;
+        const int s_end = P.step_end > 0 ? P.step_end : n_steps;
+        T* state = reinterpret_cast<T*>(P.state);
+
         T x[TPT], y[TPT], vx[TPT], vy[TPT];
         int tj[TPT], tk[TPT];
         bool act[TPT];
@@ -464,11 +469,19 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             const int tt = act[i] ? t : 0;
             tj[i] = tt / n_mu;
             tk[i] = tt - tj[i] * n_mu;
-            const T v0 = reinterpret_cast<const T*>(P.v0)[tj[i]];
-            x[i] = x0;
-            y[i] = T(0);
-            vx[i] = v0 * reinterpret_cast<const T*>(P.mu)[tk[i]];
-            vy[i] = v0 * reinterpret_cast<const T*>(P.smu)[tk[i]];
+            if (state && s_begin > 0) {          // resume a served request
+                const T* st = state + ((size_t)seg * n_seg + tt) * 4;
+                x[i] = st[0];
+                y[i] = st[1];
+                vx[i] = st[2];
+                vy[i] = st[3];
+            } else {                             // Sec. II.C initial conditions
+                const T v0 = reinterpret_cast<const T*>(P.v0)[tj[i]];
+                x[i] = x0;
+                y[i] = T(0);
+                vx[i] = v0 * reinterpret_cast<const T*>(P.mu)[tk[i]];
+                vy[i] = v0 * reinterpret_cast<const T*>(P.smu)[tk[i]];
+            }
         }
 
         // A trajectory beyond R whose position recedes along the integration
@@ -483,7 +496,7 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             f2 X = pk(x[0], x[1]), Y = pk(y[0], y[1]);
             f2 VX = pk(vx[0], vx[1]), VY = pk(vy[0], vy[1]);
             const HaloX2 h2{dup(hc.invIc), dup(-hc.invR3), hc.R2};
-            for (int n = 0; n < n_steps; ++n) {
+            for (int n = s_begin; n < s_end; ++n) {
                 const f2 r2 = fma2(X, X, mul2(Y, Y));
                 const f2 dot = fma2(X, VX, mul2(Y, VY));
                 const bool fin0 = !act[0] || (f2lo(r2) >= hc.R2 && f2lo(dot) <= 0.0f);
@@ -505,7 +518,7 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             vx[0] = f2lo(VX); vx[1] = f2hi(VX);
             vy[0] = f2lo(VY); vy[1] = f2hi(VY);
         } else {
-            for (int n = 0; n < n_steps; ++n) {
+            for (int n = s_begin; n < s_end; ++n) {
                 bool fin = true, fin_i[TPT];
 #pragma unroll
                 for (int i = 0; i < TPT; ++i) {
@@ -526,6 +539,21 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                     rk4_step<T, Ctr>(x[i], y[i], vx[i], vy[i], c, hc, ctr);
                 }
             }
+        }
+
+        if (state && s_end < n_steps) {          // more chunks follow: keep the state
+#pragma unroll
+            for (int i = 0; i < TPT; ++i) {
+                if (!act[i]) continue;
+                const int t = tis * P.tile + i * blockDim.x + threadIdx.x;
+                T* st = state + ((size_t)seg * n_seg + t) * 4;
+                st[0] = x[i];
+                st[1] = y[i];
+                st[2] = vx[i];
+                st[3] = vy[i];
+            }
+            __syncthreads();   // every thread has read s_tile before it is reused
+            continue;
         }
 
         // Liouville map and the weight of each trajectory in Eq. localdensity

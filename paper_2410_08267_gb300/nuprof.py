@@ -74,6 +74,23 @@ class nu_plan_info(C.Structure):
                 ("precision", C.c_int), ("n_steps", C.c_int)]
 
 
+class nu_server_opts(C.Structure):
+    _fields_ = [("device_bytes", C.c_size_t), ("max_active", C.c_int), ("chunk_steps", C.c_int),
+                ("precision", C.c_int), ("block", C.c_int), ("tpt", C.c_int), ("flags", C.c_int),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("gpu_timeout_ms", C.c_double)]
+
+
+class nu_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("admitted", C.c_longlong),
+                ("completed", C.c_longlong), ("cancelled", C.c_longlong),
+                ("rejected", C.c_longlong), ("iterations", C.c_longlong),
+                ("traj_steps", C.c_longlong), ("busy_ms", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("pending", C.c_int),
+                ("active", C.c_int), ("max_active_seen", C.c_int), ("status", C.c_int),
+                ("arena_bytes", C.c_longlong), ("arena_peak", C.c_longlong)]
+
+
 class nu_peaks(C.Structure):
     _fields_ = [("ffma_tflops", C.c_double), ("ffma2_tflops", C.c_double),
                 ("rsqrt_gops", C.c_double), ("lg2_gops", C.c_double),
@@ -124,6 +141,18 @@ def lib():
                                              C.c_int, P(nu_pgrid), P(nu_opts), P(C.c_double),
                                              P(C.c_double), vp]
     L.nu_profile_compute_noalloc.restype = C.c_int
+    L.nu_server_create.argtypes = [P(nu_server_opts), P(vp)]
+    L.nu_server_submit.argtypes = [vp, P(nu_cosmo), P(nu_halo), P(nu_relic), P(C.c_double), C.c_int,
+                                   P(nu_pgrid), P(nu_opts), P(C.c_longlong)]
+    L.nu_server_poll.argtypes = [vp, C.c_longlong, P(C.c_double), P(C.c_double), C.c_int,
+                                 P(C.c_double)]
+    L.nu_server_cancel.argtypes = [vp, C.c_longlong]
+    L.nu_server_stats.argtypes = [vp, P(nu_serve_stats)]
+    L.nu_server_destroy.argtypes = [vp]
+    L.nu_server_destroy.restype = None
+    for name in ("nu_server_create", "nu_server_submit", "nu_server_poll", "nu_server_cancel",
+                 "nu_server_stats"):
+        getattr(L, name).restype = C.c_int
     L.nu_measure_peaks.argtypes = [vp, P(nu_peaks)]
     L.nu_measure_peaks.restype = C.c_int
     L.nu_kernel_launches.argtypes = []
@@ -217,6 +246,56 @@ def strerror(code: int) -> str:
 
 
 nu_strerror = strerror
+
+
+def nu_server_create(device_bytes: int, precision: int = NU_MIXED, max_active: int = 0,
+                     chunk_steps: int = 100, block: int = 0, tpt: int = 0, flags: int = 0,
+                     gpu_timeout_ms: float = 0.0, torch_alloc: bool = False) -> C.c_void_p:
+    o = nu_server_opts()
+    o.device_bytes, o.max_active, o.chunk_steps, o.precision = device_bytes, max_active, chunk_steps, precision
+    o.block, o.tpt, o.flags, o.gpu_timeout_ms = block, tpt, flags, gpu_timeout_ms
+    if torch_alloc:
+        o.alloc, o.free = TORCH_ALLOC, TORCH_FREE
+    srv = C.c_void_p()
+    _check(lib().nu_server_create(C.byref(o), C.byref(srv)), "nu_server_create")
+    return srv
+
+
+def nu_server_submit(srv, pb: "W.Problem") -> int:
+    cosmo, halo, relic, radii, grid, opts = structs(pb, torch_alloc=False)
+    t = C.c_longlong()
+    _check(lib().nu_server_submit(srv, C.byref(cosmo), C.byref(halo), C.byref(relic), _dptr(radii),
+                                  len(radii), C.byref(grid), C.byref(opts), C.byref(t)),
+           "nu_server_submit")
+    return t.value
+
+
+def nu_server_poll(srv, ticket: int, n_radii: int):
+    """None while running; else (status, n/nbar, err, latency_ms)."""
+    out = np.zeros(n_radii)
+    err = np.zeros(n_radii)
+    lat = C.c_double()
+    rc = lib().nu_server_poll(srv, int(ticket), _dptr(out), _dptr(err), int(n_radii), C.byref(lat))
+    if rc == NU_EAGAIN:
+        return None
+    if rc == NU_EINVAL:
+        raise NuError(rc, "nu_server_poll")
+    return rc, out, err, lat.value
+
+
+def nu_server_cancel(srv, ticket: int):
+    _check(lib().nu_server_cancel(srv, int(ticket)), "nu_server_cancel")
+
+
+def nu_server_stats(srv) -> dict:
+    st = nu_serve_stats()
+    _check(lib().nu_server_stats(srv, C.byref(st)), "nu_server_stats")
+    return {k: getattr(st, k) for k, _ in nu_serve_stats._fields_}
+
+
+def nu_server_destroy(srv):
+    if srv:
+        lib().nu_server_destroy(srv)
 
 
 def nu_measure_peaks(stream=None) -> dict:

@@ -1,0 +1,142 @@
+"""The continuous-batching server: requests of different sizes that arrive
+while others run share launches, each result is bitwise the one the request
+gets alone, memory admission and cancellation behave, and the one-request-
+per-launch form (one slot, whole runs) gives the same results."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2410_08267_gb300 import nuprof as nu
+from paper_2410_08267_gb300 import workloads as W
+
+from gpu_common import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    return require_gpu()
+
+
+def _alone(pb, block=128, tpt=3):
+    h = nu.create(pb, block=block, tpt=tpt)
+    try:
+        nu.nu_profile_run(h)
+        return nu.nu_profile_result(h, pb.n_radii)
+    finally:
+        nu.nu_profile_destroy(h)
+
+
+def _wait(srv, ticket, n_radii, timeout=60.0):
+    t0 = time.time()
+    while time.time() - t0 < timeout:
+        r = nu.nu_server_poll(srv, ticket, n_radii)
+        if r is not None:
+            return r
+        time.sleep(0.001)
+    raise TimeoutError(ticket)
+
+
+def _stream(n, seed, max_radii=24, n_steps=200):
+    reqs = W.serving_stream(rate=1000.0, n_requests=n, seed=seed, max_radii=max_radii,
+                            n_steps=n_steps)
+    return [r.problem for r in reqs]
+
+
+@pytest.mark.parametrize("chunk", [0, 37, 100])
+def test_results_in_the_mix_are_bitwise_the_results_alone(chunk):
+    probs = _stream(10, seed=31)
+    alone = [_alone(pb) for pb in probs]
+    srv = nu.nu_server_create(device_bytes=512 << 20, chunk_steps=chunk)
+    try:
+        tickets = []
+        for i, pb in enumerate(probs):           # staggered arrivals while others run
+            tickets.append(nu.nu_server_submit(srv, pb))
+            if i % 3 == 2:
+                time.sleep(0.002)
+        for t, pb, (a, ae) in zip(tickets, probs, alone):
+            rc, out, err, lat = _wait(srv, t, pb.n_radii)
+            assert rc == nu.NU_OK and lat > 0
+            assert np.array_equal(out, a) and np.array_equal(err, ae)
+        st = nu.nu_server_stats(srv)
+        assert st["completed"] == len(probs) and st["status"] == nu.NU_OK
+        if chunk:
+            assert st["max_active_seen"] > 1        # requests shared launches
+            assert st["iterations"] < sum(-(-pb.n_steps // chunk) for pb in probs)
+    finally:
+        nu.nu_server_destroy(srv)
+
+
+def test_one_request_per_launch_form_agrees():
+    probs = _stream(4, seed=32)
+    srv = nu.nu_server_create(device_bytes=256 << 20, chunk_steps=0, max_active=1)
+    try:
+        ts = [nu.nu_server_submit(srv, pb) for pb in probs]
+        for t, pb in zip(ts, probs):
+            rc, out, _, _ = _wait(srv, t, pb.n_radii)
+            assert rc == nu.NU_OK and np.array_equal(out, _alone(pb)[0])
+        st = nu.nu_server_stats(srv)
+        assert st["iterations"] == len(probs) and st["max_active_seen"] == 1
+    finally:
+        nu.nu_server_destroy(srv)
+
+
+def test_admission_by_memory_and_refusal():
+    pb = _stream(1, seed=33, max_radii=64, n_steps=100)[0]
+    need = nu.plan(pb, block=128, tpt=3)["device_bytes"] + pb.n_traj * 16 + 4096
+    overhead = 2 * 256 * 256 + (1 << 16)          # descriptors of 256 slots, prefixes, control
+    # a budget that holds two copies at a time: the others wait for memory
+    srv = nu.nu_server_create(device_bytes=max(1 << 20, int(2.5 * need) + overhead),
+                              chunk_steps=25, max_active=256)
+    try:
+        ref = _alone(pb)[0]
+        ts = [nu.nu_server_submit(srv, pb) for _ in range(6)]
+        for t in ts:
+            rc, out, _, _ = _wait(srv, t, pb.n_radii)
+            assert rc == nu.NU_OK and np.array_equal(out, ref)
+        st = nu.nu_server_stats(srv)
+        assert st["max_active_seen"] == 2 and st["arena_peak"] <= st["arena_bytes"]
+        huge = W.plain_small(precision=W.MIXED)[0].replace(radii=np.geomspace(1, 300, 400),
+                                                          n_q=256, n_mu=64)
+        t = nu.nu_server_submit(srv, huge)         # can never fit: refused, server keeps going
+        rc, _, _, _ = _wait(srv, t, huge.n_radii)
+        assert rc == nu.NU_ENOMEM
+        t2 = nu.nu_server_submit(srv, pb)
+        assert _wait(srv, t2, pb.n_radii)[0] == nu.NU_OK
+    finally:
+        nu.nu_server_destroy(srv)
+
+
+def test_cancel_and_ticket_errors():
+    probs = _stream(6, seed=34, n_steps=400)
+    srv = nu.nu_server_create(device_bytes=256 << 20, chunk_steps=20, max_active=2)
+    try:
+        ts = [nu.nu_server_submit(srv, pb) for pb in probs]
+        nu.nu_server_cancel(srv, ts[-1])             # still queued behind two slots
+        results = [_wait(srv, t, pb.n_radii)[0] for t, pb in zip(ts, probs)]
+        assert results[-1] == nu.NU_ECANCELED
+        assert all(r == nu.NU_OK for r in results[:-1])
+        with pytest.raises(nu.NuError):
+            nu.nu_server_poll(srv, ts[0], probs[0].n_radii)     # already delivered
+        with pytest.raises(nu.NuError):
+            nu.nu_server_poll(srv, 10 ** 9, 3)                  # unknown
+        with pytest.raises(nu.NuError):
+            nu.nu_server_cancel(srv, ts[0])                     # already done
+        st = nu.nu_server_stats(srv)
+        assert st["cancelled"] == 1 and st["completed"] == len(probs) - 1
+    finally:
+        nu.nu_server_destroy(srv)
+
+
+def test_fp64_server():
+    probs = [pb.replace(precision=W.FP64) for pb in _stream(3, seed=35, n_steps=60)]
+    srv = nu.nu_server_create(device_bytes=256 << 20, precision=nu.NU_FP64, chunk_steps=25)
+    try:
+        ts = [nu.nu_server_submit(srv, pb) for pb in probs]
+        for t, pb in zip(ts, probs):
+            rc, out, _, _ = _wait(srv, t, pb.n_radii)
+            assert rc == nu.NU_OK and np.array_equal(out, _alone(pb, block=256, tpt=1)[0])
+    finally:
+        nu.nu_server_destroy(srv)
