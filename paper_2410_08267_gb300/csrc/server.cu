@@ -508,7 +508,7 @@ int nu_server_cancel(nu_server* s, long long ticket)
     {
         std::lock_guard<std::mutex> g(s->mu);
         if (ticket < 1 || ticket >= s->next_ticket) return NU_EINVAL;
-        if (s->done.count(ticket)) return NU_EINVAL;      // already finished
+        if (s->done.count(ticket) || s->delivered.count(ticket)) return NU_EINVAL;   // finished
         s->cancel_requests[ticket] = true;
     }
     s->cv.notify_one();
