@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -157,7 +158,9 @@ struct nu_server {
     std::map<long long, Done> done;
     std::set<long long> delivered;
     std::map<long long, bool> cancel_requests;
-    std::vector<Active> active;
+    std::vector<Active> active;             // on the GPU (the launch in flight)
+    std::vector<Active> staged;             // admitted, join the next launch
+    std::atomic<int> on_device{0};          // active + staged, for statistics
     long long next_ticket = 1;
     bool stop = false;
     int fatal = NU_OK;
@@ -171,6 +174,7 @@ struct nu_server {
     std::vector<double> latencies;
 
     void run();
+    bool admit_one();
     void finish(Active& a, int rc, std::vector<double>* out, std::vector<double>* err);
 };
 
@@ -183,6 +187,7 @@ void nu_server::finish(Active& a, int rc, std::vector<double>* out, std::vector<
     d.latency_ms = ms_since(a.t_submit);
     nu_profile_destroy(a.h);                 // returns its memory to the arena
     arena.release(a.state);
+    on_device.fetch_sub(1);
     std::lock_guard<std::mutex> g(mu);
     if (rc == NU_OK) {
         ++completed;
@@ -193,6 +198,62 @@ void nu_server::finish(Active& a, int rc, std::vector<double>* out, std::vector<
     done[a.ticket] = std::move(d);
 }
 
+// Admit the request at the head of the queue into `staged` if memory and
+// slots allow.  Returns true if the queue head was consumed (admitted,
+// refused or cancelled), false if it has to wait (or the queue is empty).
+bool nu_server::admit_one()
+{
+    Pending p;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (pending.empty() || (int)(active.size() + staged.size()) >= o.max_active || fatal != NU_OK)
+            return false;
+        auto c = cancel_requests.find(pending.front().ticket);
+        if (c != cancel_requests.end()) {
+            done[pending.front().ticket] = Done{NU_ECANCELED, {}, {}, ms_since(pending.front().t_submit)};
+            ++cancelled;
+            cancel_requests.erase(c);
+            pending.pop_front();
+            return true;
+        }
+        p = pending.front();
+    }
+    nu_plan_info info;
+    int rc = nu_profile_plan(&p.cosmo, &p.halo, &p.relic, p.radii.data(), (int)p.radii.size(),
+                             &p.grid, &p.opts, &info);
+    const size_t sz = o.precision == NU_FP64 ? sizeof(double) : sizeof(float);
+    const size_t state_bytes = (size_t)info.n_traj * 4 * sz;
+    if (rc == NU_OK && up256((size_t)info.device_bytes) + up256(state_bytes) > capacity)
+        rc = NU_ENOMEM;                       // can never fit: refuse
+    nu_profile* h = nullptr;
+    void* state = nullptr;
+    if (rc == NU_OK) {
+        state = arena.alloc(state_bytes);
+        if (state) rc = nu_profile_create(&p.cosmo, &p.halo, &p.relic, p.radii.data(),
+                                          (int)p.radii.size(), &p.grid, &p.opts, &h);
+        if (!state || rc == NU_ENOMEM) {
+            arena.release(state);
+            if (h) nu_profile_destroy(h);
+            if (!active.empty() || !staged.empty()) return false;   // wait for room
+            rc = NU_ENOMEM;                   // nothing to wait for: refuse
+            state = nullptr;
+            h = nullptr;
+        }
+    }
+    std::lock_guard<std::mutex> g(mu);
+    pending.pop_front();
+    if (rc != NU_OK) {
+        arena.release(state);
+        done[p.ticket] = Done{rc, {}, {}, ms_since(p.t_submit)};
+        ++rejected;
+        return true;
+    }
+    staged.push_back(Active{p.ticket, h, state, 0, profile_n_steps(h), false, p.t_submit});
+    ++admitted;
+    on_device.store((int)(active.size() + staged.size()));
+    return true;
+}
+
 void nu_server::run()
 {
     cudaSetDevice(device);
@@ -201,63 +262,21 @@ void nu_server::run()
     const bool gtab = (o.flags & NU_FLAG_GTAB) != 0;
     int slot = 0;
     for (;;) {
-        // ---- admission: first come, first served, while memory and slots allow ----
-        for (;;) {
-            Pending p;
-            {
-                std::unique_lock<std::mutex> lk(mu);
-                if (stop) return;
-                if (active.empty() && pending.empty())
-                    cv.wait_for(lk, std::chrono::milliseconds(20));
-                if (stop) return;
-                if (pending.empty() || (int)active.size() >= o.max_active || fatal != NU_OK) break;
-                auto c = cancel_requests.find(pending.front().ticket);
-                if (c != cancel_requests.end()) {
-                    Done d{NU_ECANCELED, {}, {}, ms_since(pending.front().t_submit)};
-                    done[pending.front().ticket] = d;
-                    ++cancelled;
-                    cancel_requests.erase(c);
-                    pending.pop_front();
-                    continue;
-                }
-                p = pending.front();
-            }
-            nu_plan_info info;
-            int rc = nu_profile_plan(&p.cosmo, &p.halo, &p.relic, p.radii.data(), (int)p.radii.size(),
-                                     &p.grid, &p.opts, &info);
-            const size_t sz = o.precision == NU_FP64 ? sizeof(double) : sizeof(float);
-            const size_t state_bytes = (size_t)info.n_traj * 4 * sz;
-            if (rc == NU_OK && up256((size_t)info.device_bytes) + up256(state_bytes) > capacity)
-                rc = NU_ENOMEM;                       // can never fit: refuse
-            nu_profile* h = nullptr;
-            void* state = nullptr;
-            if (rc == NU_OK) {
-                state = arena.alloc(state_bytes);
-                if (state) rc = nu_profile_create(&p.cosmo, &p.halo, &p.relic, p.radii.data(),
-                                                  (int)p.radii.size(), &p.grid, &p.opts, &h);
-                if (!state || rc == NU_ENOMEM) {
-                    arena.release(state);
-                    if (h) nu_profile_destroy(h);
-                    if (!active.empty()) break;       // no room now: wait for requests to leave
-                    rc = NU_ENOMEM;                   // nothing to wait for: refuse
-                    state = nullptr;
-                    h = nullptr;
-                }
-            }
-            std::lock_guard<std::mutex> g(mu);
-            pending.pop_front();
-            if (rc != NU_OK) {
-                arena.release(state);
-                done[p.ticket] = Done{rc, {}, {}, ms_since(p.t_submit)};
-                ++rejected;
-                continue;
-            }
-            active.push_back(Active{p.ticket, h, state, 0, profile_n_steps(h), false, p.t_submit});
-            ++admitted;
-            max_active_seen = std::max(max_active_seen, (int)active.size());
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (stop) return;
+            if (active.empty() && staged.empty() && pending.empty())
+                cv.wait_for(lk, std::chrono::milliseconds(20));
+            if (stop) return;
         }
+        // with nothing on the GPU, admit as much as fits before launching
+        if (active.empty())
+            while (admit_one()) {}
+        for (auto& a : staged) active.push_back(a);
+        staged.clear();
         {
             std::lock_guard<std::mutex> g(mu);
+            max_active_seen = std::max(max_active_seen, (int)active.size());
             for (auto& a : active) {
                 auto c = cancel_requests.find(a.ticket);
                 if (c != cancel_requests.end()) {
@@ -316,7 +335,9 @@ void nu_server::run()
         }
         const auto t_launch = Clock::now();
         if (rc == NU_OK && cudaEventRecord(ev, compute) != cudaSuccess) rc = NU_ECUDA;
-        // bounded wait for the launch (requests keep arriving meanwhile)
+        // bounded wait for the launch; requests that arrive meanwhile are
+        // admitted now (their tables upload on a separate stream) and join
+        // the next launch
         while (rc == NU_OK) {
             const cudaError_t q = cudaEventQuery(ev);
             if (q == cudaSuccess) break;
@@ -328,7 +349,7 @@ void nu_server::run()
                 rc = NU_ETIMEDOUT;
                 break;
             }
-            std::this_thread::sleep_for(std::chrono::microseconds(50));
+            if (!admit_one()) std::this_thread::sleep_for(std::chrono::microseconds(50));
         }
         const double launch_ms = ms_since(t_launch);
         slot ^= 1;
@@ -343,7 +364,9 @@ void nu_server::run()
                 // keep their memory (it may still be written)
                 std::lock_guard<std::mutex> g(mu);
                 for (auto& a : active) done[a.ticket] = Done{rc, {}, {}, ms_since(a.t_submit)};
+                for (auto& a : staged) done[a.ticket] = Done{rc, {}, {}, ms_since(a.t_submit)};
                 active.clear();
+                staged.clear();
                 return;
             }
             for (auto& a : active) finish(a, rc, nullptr, nullptr);
@@ -529,7 +552,7 @@ int nu_server_stats(nu_server* s, nu_serve_stats* out)
     out->traj_steps = s->traj_steps;
     out->busy_ms = s->busy_ms;
     out->pending = (int)s->pending.size();
-    out->active = (int)s->active.size();
+    out->active = s->on_device.load();
     out->max_active_seen = s->max_active_seen;
     out->arena_bytes = (long long)s->arena.size();
     out->arena_peak = (long long)s->arena.peak();
@@ -565,10 +588,11 @@ void nu_server_destroy(nu_server* s)
     const bool gpu_ok = s->fatal != NU_ETIMEDOUT;
     if (gpu_ok) {
         cudaStreamSynchronize(s->compute);
-        for (auto& a : s->active) {
-            nu_profile_destroy(a.h);
-            s->arena.release(a.state);
-        }
+        for (auto* list : {&s->active, &s->staged})
+            for (auto& a : *list) {
+                nu_profile_destroy(a.h);
+                s->arena.release(a.state);
+            }
     }
     // after a timeout the arena may still be in use by the GPU: it is leaked
     // rather than freed under a running kernel
