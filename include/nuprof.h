@@ -329,6 +329,9 @@ typedef struct nu_server_opts {
     nu_free_fn free;
     void* alloc_ctx;
     double gpu_timeout_ms;   /* bound on one launch (<= 0 -> 60000)               */
+    double step_budget;      /* trajectory-steps per launch (<= 0 -> 4e9): with many
+                                requests active the chunk shrinks to fit it, which
+                                bounds each launch's duration                      */
 } nu_server_opts;
 
 typedef struct nu_serve_stats {

@@ -4,6 +4,8 @@
 // trajectory kernel, and the quadrature nodes of Eq. localdensity.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "nuprof_internal.h"
 
@@ -206,7 +208,28 @@ void log_nodes(int n, double q_min, double q_max, std::vector<double>& q,
 // Gauss-Legendre rule on [-1, 1]: roots of P_n from Tricomi's asymptotic
 // estimate refined by Newton steps, with P_n and P_n' from the three-term
 // recurrence; weights 2 / ((1 - x^2) P_n'(x)^2).  Nodes ascend.
+static void gauss_legendre_compute(int n, std::vector<double>& x, std::vector<double>& w);
+
+// Rules are cached per n (requests of a scan share a few direction grids).
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w)
+{
+    static std::mutex mu;
+    static std::map<int, std::pair<std::vector<double>, std::vector<double>>> cache;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(n);
+        if (it != cache.end()) {
+            x = it->second.first;
+            w = it->second.second;
+            return;
+        }
+    }
+    gauss_legendre_compute(n, x, w);
+    std::lock_guard<std::mutex> g(mu);
+    if (cache.size() < 4096) cache[n] = {x, w};
+}
+
+static void gauss_legendre_compute(int n, std::vector<double>& x, std::vector<double>& w)
 {
     x.assign(n, 0.0);
     w.assign(n, 0.0);

@@ -175,6 +175,13 @@ struct nu_server {
 
     void run();
     bool admit_one();
+    double staged_work() const
+    {
+        double w = 0.0;
+        for (const Active& a : staged)
+            w += (double)profile_n_traj(a.h) * (o.chunk_steps > 0 ? o.chunk_steps : a.n_steps);
+        return w;
+    }
     void finish(Active& a, int rc, std::vector<double>* out, std::vector<double>* err);
 };
 
@@ -269,9 +276,13 @@ void nu_server::run()
                 cv.wait_for(lk, std::chrono::milliseconds(20));
             if (stop) return;
         }
-        // with nothing on the GPU, admit as much as fits before launching
-        if (active.empty())
-            while (admit_one()) {}
+        // with nothing on the GPU, admit requests up to one launch's budget
+        // before launching (the rest are admitted while it runs)
+        if (active.empty()) {
+            double work = 0.0;
+            while (work < o.step_budget && admit_one())
+                if (!staged.empty()) work = staged_work();
+        }
         for (auto& a : staged) active.push_back(a);
         staged.clear();
         {
@@ -297,6 +308,12 @@ void nu_server::run()
         if (active.empty()) continue;
 
         // ---- one launch: every active request advances by one chunk ----
+        // chunk: chunk_steps, shrunk so that the launch stays within step_budget
+        double traj_active = 0.0;
+        for (const Active& a : active) traj_active += (double)profile_n_traj(a.h);
+        int chunk = o.chunk_steps;
+        if (chunk > 0 && traj_active * chunk > o.step_budget)
+            chunk = std::max(1, (int)(o.step_budget / traj_active));
         std::vector<DevProblem> desc(active.size());
         std::vector<int> prefix(active.size() + 1, 0);
         long long steps_this = 0;
@@ -310,7 +327,7 @@ void nu_server::run()
             d.tiles_per_seg = (int)((seg + tile - 1) / tile);
             d.state = a.state;
             d.step_begin = a.progress;
-            d.step_end = std::min(a.n_steps, a.progress + (o.chunk_steps > 0 ? o.chunk_steps : a.n_steps));
+            d.step_end = std::min(a.n_steps, a.progress + (chunk > 0 ? chunk : a.n_steps));
             desc[i] = d;
             prefix[i + 1] = prefix[i] + d.tiles_per_seg * d.n_radii;
             steps_this += profile_n_traj(a.h) * (d.step_end - d.step_begin);
@@ -418,6 +435,7 @@ int nu_server_create(const nu_server_opts* opts, nu_server** out)
     if (o.tpt == kTptPacked && o.precision != NU_MIXED) return NU_EINVAL;
     if (o.chunk_steps < 0) return NU_EINVAL;
     if (o.gpu_timeout_ms <= 0.0) o.gpu_timeout_ms = 60000.0;
+    if (o.step_budget <= 0.0) o.step_budget = 4e9;
     if (o.device_bytes < ((size_t)1 << 20)) return NU_EINVAL;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         cudaGetLastError();
