@@ -397,19 +397,23 @@ void nu_server::run()
             busy_ms += launch_ms;
         }
         // ---- retire the requests that reached their last step ----
-        for (size_t i = 0; i < active.size();) {
-            Active& a = active[i];
+        // (desc[i] describes active[i] of this launch; build the survivors in a
+        // new list so that the two stay paired while requests leave)
+        std::vector<Active> keep;
+        keep.reserve(active.size());
+        for (size_t i = 0; i < active.size(); ++i) {
+            Active a = active[i];
             a.progress = desc[i].step_end;
             if (a.progress < a.n_steps) {
-                ++i;
+                keep.push_back(a);
                 continue;
             }
             const int nr = profile_n_radii(a.h);
             std::vector<double> out(nr), err(nr);
             const int r = profile_read(a.h, out.data(), err.data(), upload);
             finish(a, r, &out, &err);
-            active.erase(active.begin() + i);
         }
+        active.swap(keep);
     }
 }
 

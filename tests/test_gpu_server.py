@@ -69,6 +69,31 @@ def test_results_in_the_mix_are_bitwise_the_results_alone(chunk):
         nu.nu_server_destroy(srv)
 
 
+def test_requests_joining_at_different_iterations_with_different_lengths():
+    """Requests enter while others are part-way through (different progress
+    and step counts in one launch) and leave at different launches."""
+    probs = _stream(12, seed=36, max_radii=16, n_steps=120)
+    probs = [pb.replace(n_steps=(60, 120, 180, 240)[i % 4]) for i, pb in enumerate(probs)]
+    alone = [_alone(pb)[0] for pb in probs]
+    srv = nu.nu_server_create(device_bytes=512 << 20, chunk_steps=13)
+    try:
+        tickets = []
+        for pb in probs:
+            tickets.append(nu.nu_server_submit(srv, pb))
+            it0 = nu.nu_server_stats(srv)["iterations"]
+            t0 = time.time()                      # let at least one launch pass
+            while nu.nu_server_stats(srv)["iterations"] == it0 and time.time() - t0 < 5:
+                time.sleep(0.0005)
+        for t, pb, a in zip(tickets, probs, alone):
+            rc, out, _, _ = _wait(srv, t, pb.n_radii)
+            assert rc == nu.NU_OK and np.array_equal(out, a)
+        st = nu.nu_server_stats(srv)
+        assert st["traj_steps"] == sum(pb.traj_steps for pb in probs)
+        assert st["max_active_seen"] > 2
+    finally:
+        nu.nu_server_destroy(srv)
+
+
 def test_one_request_per_launch_form_agrees():
     probs = _stream(4, seed=32)
     srv = nu.nu_server_create(device_bytes=256 << 20, chunk_steps=0, max_active=1)
