@@ -9,9 +9,9 @@ mixed precision (FP32 state and force, FP64-built tables, FP64 sums).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  Under torchrun each rank runs its own copy of
-the workload on its own GPU (weak scaling, no data-path collective); the
-timing is the max over ranks.  --impl reference times the FP64 CPU oracle on
+Prints one JSON line (rank 0).  Under torchrun the job is N copies of the
+workload whose requests are partitioned over the N ranks (weak scaling, no
+data-path collective); the timing is the max over ranks.  --impl reference times the FP64 CPU oracle on
 a bounded sample of the same workload on the host cores.
 """
 from __future__ import annotations
@@ -56,6 +56,12 @@ FLOPS_EVAL = (3, 8, 15, 15)
 FLOPS_COMBINE = 61
 FLOPS_FULL = 121
 SMS, FP32_LANES_PER_SM = 152, 128
+# DRAM bytes (read + write) per launch of the trajectory kernel at the tuned
+# shape 128x3xg on this workload: mean of two launches of one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), recorded in
+# profiles/traj_kernel_precision_sweep_mixed.md.  Must be reset to None
+# whenever the kernel changes, until it is captured again.
+NCU_TRAFFIC_BYTES = {"128x3xg": 688640.0}
 SAMPLE_RADII = (0, 21, 42, 63)
 SAMPLE_MASS_INDEX = 2          # 0.1 eV
 
@@ -220,12 +226,21 @@ def bench_ours(args):
     __graft_entry__.build()
     from paper_2410_08267_gb300 import nuprof as nu
 
+    from paper_2410_08267_gb300 import sharding
+
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
-    problems = W.precision_sweep(precision=W.MIXED)
+    one = W.precision_sweep(precision=W.MIXED)
     if args.case == "small":            # profiling case: one mass, 24 radii (fills every SM)
-        problems = [problems[SAMPLE_MASS_INDEX].replace(radii=np.geomspace(1.0, 1000.0, 24))]
+        one = [one[SAMPLE_MASS_INDEX].replace(radii=np.geomspace(1.0, 1000.0, 24))]
+    # The job at N GPUs is N copies of the workload (weak scaling); its
+    # requests are partitioned over the ranks by trajectory-steps, with no
+    # collective on the data path.
+    job = one * world
+    mine = sharding.partition_problems(job, world)[rank]
+    problems = [job[i] for i in mine]
     traj_steps = sum(pb.traj_steps for pb in problems)
+    job_traj_steps = sum(pb.traj_steps for pb in job)
 
     with torch.cuda.stream(stream):
         hs = [nu.create(pb, stream=stream) for pb in problems]
@@ -272,17 +287,15 @@ def bench_ours(args):
     grid = nu.nu_batch_info(batch)["grid"]
     counts = nu.nu_batch_branch_counts(batch, stream)     # untimed counting run
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms_total = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = sharding.max_over_ranks(float(sum(step_ms)), dist)
     ms_per_step = ms_total / args.steps
-    value = traj_steps * world / (ms_per_step / 1e3)
+    value = job_traj_steps / (ms_per_step / 1e3)
     clock = clocks.summary()
 
-    # results of the last timed run (for the accuracy record)
-    results = [nu.nu_profile_result(h, pb.n_radii)[0] for h, pb in zip(hs, problems)]
+    # results of the last timed run, gathered in job order (for the accuracy record)
+    results = sharding.gather_profiles(
+        {i: nu.nu_profile_result(h, pb.n_radii)[0] for i, h, pb in zip(mine, hs, problems)},
+        len(job), dist)
 
     # ---- end to end through the public API with host buffers ----
     e2e_steps = max(2, min(args.steps, 5))
@@ -303,7 +316,7 @@ def bench_ours(args):
             for h in hh:
                 nu.nu_profile_destroy(h)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = sharding.max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist)
     for pb in problems:
         h2d += nu.plan(pb)["h2d_bytes"]
         d2h += 2 * 8 * pb.n_radii
@@ -334,7 +347,8 @@ def bench_ours(args):
     peak_mhz = clock["sm_max_mhz"] or 2070.0
     peak = fp32_peak_tflops(peak_mhz)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC_BYTES.get(f"{block}x{tpt}{'xg' if tflags else ''}"),
                 "kernel": f"traj_kernel<float,{min(tpt, 2)},packed={tpt == 3},l1_table={bool(tflags)}>",
                 "kernel_ms": kms,
                 "flops_per_launch": flops, "flops_per_executed_traj_step": flops / live_steps,
@@ -363,7 +377,7 @@ def bench_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_USED, "traj_steps_per_step": traj_steps,
+            "config": {"workload": WORKLOAD_USED, "traj_steps_per_step": job_traj_steps,
                        "precision": "mixed: FP32 state/force, FP64 tables and sums",
                        "l2": "flushed (256 MiB write) between timed steps",
                        "launch": f"one persistent batched launch per step: grid {grid} CTAs x {block} "
@@ -372,9 +386,10 @@ def bench_ours(args):
                        "autotune": (None if tune is None else
                                     {f"{b_}x{t_}{'xg' if f_ else ''}": round(ms, 4)
                                      for b_, t_, f_, ms in tune["candidates"]}),
-                       "parallelism": f"replicas x{world}"},
-            "e2e": {"value": traj_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h,
+                       "parallelism": (f"{world} ranks, each {len(one)} requests of a job of {world} "
+                                       "copies of the workload (partitioned, no collective)")},
+            "e2e": {"value": job_traj_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d * world,
+                    "d2h_bytes_per_step": d2h * world,
                     "path": "create (host tables -> device) + batch + run + result + destroy"},
             "gpu_launches": launches, "wall_s": wall, "serving": serving,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clock,
