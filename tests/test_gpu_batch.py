@@ -159,3 +159,31 @@ def test_table_through_l1_is_bitwise_the_staged_table():
                     nu.nu_profile_destroy(h)
         for a, c in zip(*outs):
             assert np.array_equal(a, c)
+
+
+def test_new_physics_batch_against_oracle():
+    """Relic kinds and a time-dependent coupling in one batch (Sec. IV.B):
+    one halo of each distribution variant at the full 128 x 256 x 64 grid,
+    compared on sampled radii."""
+    allp = W.new_physics(n_halos=256, seed=2411)
+    picks, seen = [], set()
+    for pb in allp:
+        key = (pb.f_kind, pb.f_p[0])
+        if key not in seen:
+            seen.add(key)
+            picks.append(pb)
+    assert len(picks) == 4
+    hs = [nu.create(pb) for pb in picks]
+    b = nu.nu_batch_create(hs)
+    try:
+        nu.nu_batch_run(b)
+        for h, pb in zip(hs, picks):
+            got = nu.nu_profile_result(h, pb.n_radii)[0]
+            assert np.all(np.isfinite(got))
+            sel = [0, pb.n_radii // 2, pb.n_radii - 1]
+            assert_parity(got, pb, sel=sel, where=f"new physics f={pb.f_kind}/{pb.f_p[0]}",
+                          conditioned_only=(pb.f_kind == W.F_FREEZEIN))
+    finally:
+        nu.nu_batch_destroy(b)
+        for h in hs:
+            nu.nu_profile_destroy(h)
