@@ -106,7 +106,8 @@ extern "C" {
 #define NU_FLAG_GTAB     8 /* batches: read the per-step coefficient table in
                               place through the L1 cache instead of staging it
                               in shared memory (frees shared memory, so more
-                              CTAs fit on an SM); results are identical        */
+                              CTAs fit on an SM); results are identical.  A
+                              table larger than 227 KB is always read this way */
 
 typedef struct nu_cosmo {
     double Om;       /* matter density today; Omega_Lambda = 1 - Om (Sec. II.A) */
@@ -152,7 +153,7 @@ typedef struct nu_opts {
     int block;           /* threads per CTA: 0 (default 256) or 64..512, multiple of 32 */
     int tpt;             /* trajectories per thread: 0 (default 1), 1, 2, or 3 =
                             two per thread in packed FP32x2 arithmetic (mixed
-                            precision, n_steps <= 1760; results bitwise those of 2) */
+                            precision; results bitwise those of 2)             */
     int flags;           /* NU_FLAG_*                                             */
     nu_alloc_fn alloc;
     nu_free_fn free;
@@ -160,7 +161,10 @@ typedef struct nu_opts {
     void* stream;        /* cudaStream_t used for uploads during create           */
 } nu_opts;
 
-#define NU_MAX_STEPS 3000  /* the per-step coefficient table lives in shared memory */
+#define NU_MAX_STEPS 3000  /* the per-step coefficient table (80 B per step in FP32,
+                              160 B in FP64 and in the packed path) is staged in
+                              shared memory when it fits in 227 KB and read
+                              through the L1 cache otherwise                     */
 
 typedef struct nu_profile nu_profile;
 typedef struct nu_batch nu_batch;
@@ -269,7 +273,8 @@ NU_API int nu_batch_kernel_ms(nu_batch* b, float* ms);
  * trajectory-steps integrated.  A trajectory is finished once it lies beyond R
  * and recedes along the integration direction: no later step changes its
  * velocity, so its remaining steps are not needed work (its warp stops when
- * all of its lanes are finished).  The force is data dependent (App. A has
+ * all of its lanes are finished; the test runs every 4 steps, so up to 3 steps
+ * past the finish are counted).  The force is data dependent (App. A has
  * three branches), so these counts turn one run into an exact algorithmic flop
  * count.  counts must hold 5 values.  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
 NU_API int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts);

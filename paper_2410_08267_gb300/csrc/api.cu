@@ -539,7 +539,6 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
     }
     if (b->tpt == kTptPacked && b->precision != NU_MIXED) return NU_EINVAL;
     for (int i = 0; i < n; ++i) {
-        if (b->tpt == kTptPacked && hs[i]->opts.n_steps > 1760) return NU_ENOTSUP;
         b->smem = std::max(b->smem, coef_smem_bytes(b->precision, hs[i]->opts.n_steps, b->tpt));
     }
     const int tile = b->block * traj_per_thread(b->tpt);

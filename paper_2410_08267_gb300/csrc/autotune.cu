@@ -130,7 +130,7 @@ extern "C" int nu_autotune(nu_profile* const* hs, int n, void* stream, const cha
     float best = 1e30f;
     int slot = 0;
     for (int c = 0; c < kNumShapes; ++c) {
-        if (kShapes[c].tpt == 3 && (precision != NU_MIXED || max_steps > 1760)) continue;
+        if (kShapes[c].tpt == 3 && precision != NU_MIXED) continue;
         nu_opts o;
         std::memset(&o, 0, sizeof(o));
         o.block = kShapes[c].block;

@@ -2,6 +2,7 @@
 // halo derivation of Sec. II.B, the background of Sec. II.A, the growth and
 // coupling variants of Sec. IV, the per-step coefficient table consumed by the
 // trajectory kernel, and the quadrature nodes of Eq. localdensity.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -48,8 +49,6 @@ int validate(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
     if (o->block < 64 || o->block > 512 || (o->block % 32) != 0) return NU_EINVAL;
     if (o->tpt != 1 && o->tpt != 2 && o->tpt != kTptPacked) return NU_EINVAL;
     if (o->tpt == kTptPacked && o->precision != NU_MIXED) return NU_EINVAL;
-    // the packed path stages 128 bytes per step in shared memory
-    if (o->tpt == kTptPacked && o->n_steps > 1760) return NU_ENOTSUP;
     long long ntraj = (long long)g->n_q * g->n_mu;
     if (ntraj > (1LL << 30) || (long long)n_radii * ntraj > (1LL << 40)) return NU_EINVAL;
     return NU_OK;
@@ -143,7 +142,9 @@ void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, in
         const double F = kG * coupling_kappa(halo, z) * zp1 * growth_xi(halo, d, z) * halo.M_h;
         BF = F / H;
         S = d.r_s > 0.0 ? 1.0 / (zp1 * d.r_s) : 0.0;
-        const double rin = d.r200 * zp1;
+        // the NFW part ends at r200 (1+z), and nothing acts beyond R, so the
+        // edge never exceeds R (it reaches R only at z >= z_i)
+        const double rin = std::min(d.r200 * zp1, d.R);
         Q = rin * rin;
     };
     for (int n = 0; n < n_steps; ++n) {
@@ -168,6 +169,10 @@ void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, in
         t[C_Q0] = Qa;
         t[C_Q1] = Qm;
         t[C_Q2] = Qb;
+        t[C_T0] = Sa / d.Ic;
+        t[C_T1] = Sm / d.Ic;
+        t[C_T2] = Sb / d.Ic;
+        t[C_PAD] = 0.0;
     }
 }
 

@@ -32,12 +32,22 @@ enum CoefSlot {
     C_S0,        // 1/((1+z_a) r_s)      NFW argument scale
     C_S1,        // 1/((1+z_m) r_s)
     C_S2,        // 1/((1+z_b) r_s)
-    C_Q0,        // (r200 (1+z_a))^2     squared comoving edge of the NFW part
+    C_Q0,        // min(r200 (1+z_a), R)^2   squared comoving edge of the NFW part
     C_Q1,
     C_Q2,
+    C_T0,        // S(z_a) / I(c)        with rs = S/r: y = r^2 rs, S^2/(I(c) r) = rs T
+    C_T1,
+    C_T2,
+    C_PAD,       // zero (keeps a step at a multiple of 16 bytes)
     C_COUNT
 };
-static_assert(C_COUNT == 16, "coefficient table layout");
+static_assert(C_COUNT == 20, "coefficient table layout");
+static_assert(C_COUNT % 4 == 0, "a step of the FP32 table is whole 16-byte words");
+
+// Largest dynamic shared memory of one CTA (GB300: 227 KB).  A table that does
+// not fit is read through the L1 cache instead of being staged (same values,
+// same results).
+constexpr size_t kMaxStagedSmem = 232448;
 
 // Halo and background quantities derived on the host in FP64 (Sec. II.B).
 struct Derived {

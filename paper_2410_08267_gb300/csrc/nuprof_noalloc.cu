@@ -13,6 +13,7 @@
 // call performs no heap allocation either.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -75,7 +76,7 @@ void coef_table_into(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& 
             A[s] = zp1 * zp1 / H;
             BF[s] = kG * coupling_kappa(halo, z) * zp1 * growth_xi(halo, d, z) * halo.M_h / H;
             S[s] = d.r_s > 0.0 ? 1.0 / (zp1 * d.r_s) : 0.0;
-            const double rin = d.r200 * zp1;
+            const double rin = std::min(d.r200 * zp1, d.R);   // edge never beyond R
             Q[s] = rin * rin;
         }
         double* t = tab + (size_t)n * C_COUNT;
@@ -95,6 +96,10 @@ void coef_table_into(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& 
         t[C_Q0] = Q[0];
         t[C_Q1] = Q[1];
         t[C_Q2] = Q[2];
+        t[C_T0] = S[0] / d.Ic;
+        t[C_T1] = S[1] / d.Ic;
+        t[C_T2] = S[2] / d.Ic;
+        t[C_PAD] = 0.0;
     }
 }
 

@@ -65,24 +65,26 @@ __device__ __forceinline__ float rcp_approx(float v)
 // so I = y^2 P(y) with a degree-9 polynomial P fitted to I/y^2 on [0, 1]
 // (nfw_poly_fit.py; 3.5e-7 relative in float32 Horner).  Above, the terms
 // differ by more than a factor 1.5 and are subtracted directly, with the
-// hardware base-2 logarithm and reciprocal.
-__device__ __forceinline__ float nfw_I(float y)
+// hardware base-2 logarithm and reciprocal (rcp(-u) = -1/u exactly).
+__device__ __forceinline__ float nfw_P(float y)
 {
-    if (y < 1.0f) {
-        float p = -1.933632977e-02f;
-        p = fmaf(p, y, 1.171014905e-01f);
-        p = fmaf(p, y, -3.268344104e-01f);
-        p = fmaf(p, y, 5.741083622e-01f);
-        p = fmaf(p, y, -7.448884845e-01f);
-        p = fmaf(p, y, 8.059346676e-01f);
-        p = fmaf(p, y, -7.959684730e-01f);
-        p = fmaf(p, y, 7.496873736e-01f);
-        p = fmaf(p, y, -6.666569710e-01f);
-        p = fmaf(p, y, 4.999999404e-01f);
-        return (y * y) * p;
-    }
+    float p = -1.933632977e-02f;
+    p = fmaf(p, y, 1.171014905e-01f);
+    p = fmaf(p, y, -3.268344104e-01f);
+    p = fmaf(p, y, 5.741083622e-01f);
+    p = fmaf(p, y, -7.448884845e-01f);
+    p = fmaf(p, y, 8.059346676e-01f);
+    p = fmaf(p, y, -7.959684730e-01f);
+    p = fmaf(p, y, 7.496873736e-01f);
+    p = fmaf(p, y, -6.666569710e-01f);
+    p = fmaf(p, y, 4.999999404e-01f);
+    return p;
+}
+
+__device__ __forceinline__ float nfw_I_log(float y)
+{
     const float u = 1.0f + y;
-    return fmaf(lg2_approx(u), 0.693147180559945309f, -y * rcp_approx(u));
+    return fmaf(lg2_approx(u), 0.693147180559945309f, y * rcp_approx(-u));
 }
 
 // Same in FP64, accurate to a few ulp for every y.  With t = y/(1+y),
@@ -100,6 +102,9 @@ __device__ __forceinline__ double nfw_I(double y)
     }
     return log1p(y) - t;
 }
+
+// Steps between two tests of the early exit (a power of two).
+constexpr int kExitEvery = 4;
 
 struct HaloF32 { float invIc, invR3, R2; };
 struct HaloF64 { double invIc, invR3, R2; };
@@ -129,24 +134,39 @@ struct Tally {
 // enters inside r200 (1+z): both tests are branches, so a warp whose lanes
 // are all beyond R (or all in the shell) skips that work.  The result is the
 // same value the full expression gives (0, resp. sel = 1).
+//
+// FP32 arithmetic of one evaluation, fixed per branch so that every code path
+// (scalar, packed, any warp composition) gives a lane the same bits.  With
+// rs = S/r and the table's T = S/I(c) (so y = r S = r^2 rs):
+//   beyond R:              m = 0
+//   NFW, y < 1:            m = P(y) (rs T) - 1/R^3
+//                          (I rinv^3 / I(c) = y^2 P rinv^3 / I(c) = P S^2 rinv / I(c))
+//   NFW, y >= 1, or shell: m = sel rinv^3 - 1/R^3,  sel = I(y)/I(c) or 1
+// The table guarantees Q <= R^2, so r^2 < Q implies r^2 < R^2.
 template <class Ctr = NoTally>
-__device__ __forceinline__ float accel_m(float x, float y, float S, float Q, const HaloF32& hc,
-                                         Ctr& ctr)
+__device__ __forceinline__ float accel_m(float x, float y, float S, float Q, float T,
+                                         const HaloF32& hc, Ctr& ctr)
 {
     const float r2 = fmaf(x, x, y * y);
     float m = 0.0f;
     if (r2 < hc.R2) {
         const float rinv = rsqrt_approx(fmaxf(r2, 1e-20f));   // r -> 0 guard (below 1e-10 kpc)
-        const float rinv3 = rinv * rinv * rinv;
-        float sel = 1.0f;
-        if (r2 < Q) {
-            const float ys = (r2 * rinv) * S;
-            ctr.add(ys < 1.0f ? 2 : 3);
-            sel = nfw_I(ys) * hc.invIc;
+        const float rs = rinv * S;
+        const float ys = r2 * rs;
+        if (r2 < Q && ys < 1.0f) {
+            ctr.add(2);
+            m = fmaf(nfw_P(ys), rs * T, -hc.invR3);
         } else {
-            ctr.add(1);
+            const float rinv3 = (rinv * rinv) * rinv;
+            float sel = 1.0f;
+            if (r2 < Q) {
+                ctr.add(3);
+                sel = nfw_I_log(ys) * hc.invIc;
+            } else {
+                ctr.add(1);
+            }
+            m = fmaf(sel, rinv3, -hc.invR3);
         }
-        m = fmaf(sel, rinv3, -hc.invR3);
     } else {
         ctr.add(0);
     }
@@ -154,7 +174,7 @@ __device__ __forceinline__ float accel_m(float x, float y, float S, float Q, con
 }
 
 template <class Ctr = NoTally>
-__device__ __forceinline__ double accel_m(double x, double y, double S, double Q,
+__device__ __forceinline__ double accel_m(double x, double y, double S, double Q, double,
                                           const HaloF64& hc, Ctr& ctr)
 {
     const double r2 = fma(x, x, y * y);
@@ -229,22 +249,22 @@ template <typename T, class Ctr>
 __device__ __forceinline__ void rk4_step(T& x, T& y, T& vx, T& vy, const T* c,
                                          const typename PrecTraits<T>::Halo& hc, Ctr& ctr)
 {
-    const T m1 = accel_m(x, y, c[C_S0], c[C_Q0], hc, ctr);
+    const T m1 = accel_m(x, y, c[C_S0], c[C_Q0], c[C_T0], hc, ctr);
     const T p1 = c[C_B1] * m1;
     const T X2 = fmaT(c[C_MA1], vx, x), Y2 = fmaT(c[C_MA1], vy, y);
     const T VX2 = fmaT(p1, x, vx), VY2 = fmaT(p1, y, vy);
 
-    const T m2 = accel_m(X2, Y2, c[C_S1], c[C_Q1], hc, ctr);
+    const T m2 = accel_m(X2, Y2, c[C_S1], c[C_Q1], c[C_T1], hc, ctr);
     const T p2 = c[C_B2] * m2;
     const T X3 = fmaT(c[C_MA2], VX2, x), Y3 = fmaT(c[C_MA2], VY2, y);
     const T VX3 = fmaT(p2, X2, vx), VY3 = fmaT(p2, Y2, vy);
 
-    const T m3 = accel_m(X3, Y3, c[C_S1], c[C_Q1], hc, ctr);
+    const T m3 = accel_m(X3, Y3, c[C_S1], c[C_Q1], c[C_T1], hc, ctr);
     const T p3 = c[C_B3] * m3;
     const T X4 = fmaT(c[C_MA3], VX3, x), Y4 = fmaT(c[C_MA3], VY3, y);
     const T VX4 = fmaT(p3, X3, vx), VY4 = fmaT(p3, Y3, vy);
 
-    const T m4 = accel_m(X4, Y4, c[C_S2], c[C_Q2], hc, ctr);
+    const T m4 = accel_m(X4, Y4, c[C_S2], c[C_Q2], c[C_T2], hc, ctr);
     const T p4 = c[C_B4] * m4;
 
     // x' = x - (h/6) (A_a v + 2 A_m V2 + 2 A_m V3 + A_b V4)
@@ -319,8 +339,8 @@ struct HaloX2 {
     float R2;
 };
 
-// I(y) on the polynomial branch for both lanes (see nfw_I).
-__device__ __forceinline__ f2 nfw_I_poly_x2(f2 y)
+// P(y) = I(y)/y^2 on the polynomial branch for both lanes (see nfw_P).
+__device__ __forceinline__ f2 nfw_P_x2(f2 y)
 {
     f2 p = dup(-1.933632977e-02f);
     p = fma2(p, y, dup(1.171014905e-01f));
@@ -332,54 +352,91 @@ __device__ __forceinline__ f2 nfw_I_poly_x2(f2 y)
     p = fma2(p, y, dup(7.496873736e-01f));
     p = fma2(p, y, dup(-6.666569710e-01f));
     p = fma2(p, y, dup(4.999999404e-01f));
-    return mul2(mul2(y, y), p);
+    return p;
 }
 
-// m = Mhat/r^3 for both lanes, the values of accel_m (FP32) lane by lane.
-__device__ __forceinline__ f2 accel_m_x2(f2 x, f2 y, f2 S, f2 Q, const HaloX2& hc)
+// I(y) on the logarithm branch for both lanes (see nfw_I_log).
+__device__ __forceinline__ f2 nfw_I_log_x2(f2 y)
+{
+    const f2 u = add2(dup(1.0f), y);
+    const float ua = f2lo(u), ub = f2hi(u);
+    const f2 lg = pk(lg2_approx(ua), lg2_approx(ub));
+    const f2 rn = pk(rcp_approx(-ua), rcp_approx(-ub));
+    return fma2(lg, dup(0.693147180559945309f), mul2(y, rn));
+}
+
+// m = Mhat/r^3 for both lanes: lane by lane the values of accel_m (FP32).
+// Warp-uniform paths: every lane on the polynomial branch of the NFW part
+// (the common case), every lane on its logarithm branch, or any mix (each
+// branch evaluated for both lanes and selected per lane).  All lanes of the
+// warp execute this function together (the integration loop is warp-uniform).
+__device__ __forceinline__ f2 accel_m_x2(f2 x, f2 y, f2 S, f2 Q, f2 T, const HaloX2& hc)
 {
     const f2 r2 = fma2(x, x, mul2(y, y));
     const float r2a = f2lo(r2), r2b = f2hi(r2);
     const f2 rinv = pk(rsqrt_approx(fmaxf(r2a, 1e-20f)), rsqrt_approx(fmaxf(r2b, 1e-20f)));
-    const f2 rinv3 = mul2(mul2(rinv, rinv), rinv);
-    const f2 ys = mul2(mul2(r2, rinv), S);
+    const f2 rs = mul2(rinv, S);
+    const f2 ys = mul2(r2, rs);
     const float ya = f2lo(ys), yb = f2hi(ys);
-    f2 I;
-    if (ya < 1.0f && yb < 1.0f) I = nfw_I_poly_x2(ys);
-    else I = pk(nfw_I(ya), nfw_I(yb));
-    const f2 Iq = mul2(I, hc.invIc);
-    const float sa = r2a < f2lo(Q) ? f2lo(Iq) : 1.0f;
-    const float sb = r2b < f2hi(Q) ? f2hi(Iq) : 1.0f;
-    const f2 m = fma2(pk(sa, sb), rinv3, hc.neg_invR3);
-    return pk(r2a < hc.R2 ? f2lo(m) : 0.0f, r2b < hc.R2 ? f2hi(m) : 0.0f);
+    const bool na = r2a < f2lo(Q), nb = r2b < f2hi(Q);          // inside the NFW edge
+    const bool pa = na && ya < 1.0f, pb = nb && yb < 1.0f;     // polynomial branch
+    if (__all_sync(0xffffffffu, pa && pb))
+        return fma2(nfw_P_x2(ys), mul2(rs, T), hc.neg_invR3);
+    const f2 rinv3 = mul2(mul2(rinv, rinv), rinv);
+    if (__all_sync(0xffffffffu, na && nb && !pa && !pb))
+        return fma2(mul2(nfw_I_log_x2(ys), hc.invIc), rinv3, hc.neg_invR3);
+    const f2 mp = fma2(nfw_P_x2(ys), mul2(rs, T), hc.neg_invR3);
+    const f2 Iq = mul2(nfw_I_log_x2(ys), hc.invIc);
+    const f2 ml = fma2(pk(na ? f2lo(Iq) : 1.0f, nb ? f2hi(Iq) : 1.0f), rinv3, hc.neg_invR3);
+    return pk(pa ? f2lo(mp) : (r2a < hc.R2 ? f2lo(ml) : 0.0f),
+              pb ? f2hi(mp) : (r2b < hc.R2 ? f2hi(ml) : 0.0f));
 }
 
-// rk4_step for two trajectories at once; cq holds the step's 8 x 16 bytes of
-// the duplicated table (slot j -> floats 2j, 2j+1).
-__device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const ulonglong2 (&cq)[8],
+// One 16-byte entry of the duplicated table (two slots, each a {c, c} pair).
+template <bool GTAB>
+__device__ __forceinline__ ulonglong2 coef_pair(const uint4* src4, int q)
+{
+    const uint4 w = GTAB ? __ldg(&src4[q]) : src4[q];
+    return make_ulonglong2(((unsigned long long)w.y << 32) | w.x,
+                           ((unsigned long long)w.w << 32) | w.z);
+}
+
+// rk4_step for two trajectories at once.  src4 points at the step's 10 x 16
+// bytes of the duplicated table (slot j -> floats 2j, 2j+1); each entry is
+// loaded where it is first needed, which keeps the table out of registers.
+template <bool GTAB>
+__device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const uint4* src4,
                                             const HaloX2& hc)
 {
-    const ulonglong2 q0 = cq[0], q1 = cq[1], q2 = cq[2], q3 = cq[3];
-    const ulonglong2 q4 = cq[4], q5 = cq[5], q6 = cq[6], q7 = cq[7];
-    const f2 MA1{q0.x}, MA2{q0.y}, MA3{q1.x}, B1{q1.y}, B2{q2.x}, B3{q2.y}, B4{q3.x}, W0{q3.y};
-    const f2 W1{q4.x}, W2{q4.y}, S0{q5.x}, S1{q5.y}, S2{q6.x}, Q0{q6.y}, Q1{q7.x}, Q2{q7.y};
-
-    const f2 m1 = accel_m_x2(x, y, S0, Q0, hc);
+    const ulonglong2 q5 = coef_pair<GTAB>(src4, 5), q6 = coef_pair<GTAB>(src4, 6);
+    const ulonglong2 q8 = coef_pair<GTAB>(src4, 8);
+    const f2 S0{q5.x}, S1{q5.y}, S2{q6.x}, Q0{q6.y}, T0{q8.x}, T1{q8.y};
+    const f2 m1 = accel_m_x2(x, y, S0, Q0, T0, hc);
+    const ulonglong2 q0 = coef_pair<GTAB>(src4, 0), q1 = coef_pair<GTAB>(src4, 1);
+    const f2 MA1{q0.x}, MA2{q0.y}, MA3{q1.x}, B1{q1.y};
     const f2 p1 = mul2(B1, m1);
     const f2 X2 = fma2(MA1, vx, x), Y2 = fma2(MA1, vy, y);
     const f2 VX2 = fma2(p1, x, vx), VY2 = fma2(p1, y, vy);
 
-    const f2 m2 = accel_m_x2(X2, Y2, S1, Q1, hc);
+    const ulonglong2 q7 = coef_pair<GTAB>(src4, 7);
+    const f2 Q1{q7.x}, Q2{q7.y};
+    const f2 m2 = accel_m_x2(X2, Y2, S1, Q1, T1, hc);
+    const ulonglong2 q2 = coef_pair<GTAB>(src4, 2);
+    const f2 B2{q2.x}, B3{q2.y};
     const f2 p2 = mul2(B2, m2);
     const f2 X3 = fma2(MA2, VX2, x), Y3 = fma2(MA2, VY2, y);
     const f2 VX3 = fma2(p2, X2, vx), VY3 = fma2(p2, Y2, vy);
 
-    const f2 m3 = accel_m_x2(X3, Y3, S1, Q1, hc);
+    const f2 m3 = accel_m_x2(X3, Y3, S1, Q1, T1, hc);
     const f2 p3 = mul2(B3, m3);
     const f2 X4 = fma2(MA3, VX3, x), Y4 = fma2(MA3, VY3, y);
     const f2 VX4 = fma2(p3, X3, vx), VY4 = fma2(p3, Y3, vy);
 
-    const f2 m4 = accel_m_x2(X4, Y4, S2, Q2, hc);
+    const ulonglong2 q9 = coef_pair<GTAB>(src4, 9);
+    const f2 T2{q9.x};
+    const f2 m4 = accel_m_x2(X4, Y4, S2, Q2, T2, hc);
+    const ulonglong2 q3 = coef_pair<GTAB>(src4, 3), q4 = coef_pair<GTAB>(src4, 4);
+    const f2 B4{q3.x}, W0{q3.y}, W1{q4.x}, W2{q4.y};
     const f2 p4 = mul2(B4, m4);
 
     const f2 nx = fma2(W2, VX4, fma2(W1, add2(VX2, VX3), fma2(W0, vx, x)));
@@ -489,7 +546,9 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         // re-enters: the gradient is exactly zero there (mass compensation),
         // so every later step leaves v unchanged and q_i depends on v alone.
         // A warp stops integrating once all of its lanes are in that state
-        // (padding lanes of a ragged tile start finished).  All lanes of the
+        // (padding lanes of a ragged tile start finished); the test runs every
+        // kExitEvery steps, and a finished lane that keeps stepping with its
+        // warp stays beyond R with its velocity unchanged.  All lanes of the
         // warp reach the vote, so the full mask is valid.
         if constexpr (PACKED) {
             static_assert(TPT == 2, "packed path holds two trajectories");
@@ -497,37 +556,37 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             f2 VX = pk(vx[0], vx[1]), VY = pk(vy[0], vy[1]);
             const HaloX2 h2{dup(hc.invIc), dup(-hc.invR3), hc.R2};
             for (int n = s_begin; n < s_end; ++n) {
-                const f2 r2 = fma2(X, X, mul2(Y, Y));
-                const f2 dot = fma2(X, VX, mul2(Y, VY));
-                const bool fin0 = !act[0] || (f2lo(r2) >= hc.R2 && f2lo(dot) <= 0.0f);
-                const bool fin1 = !act[1] || (f2hi(r2) >= hc.R2 && f2hi(dot) <= 0.0f);
-                done |= fin0 && fin1;
-                if (__all_sync(0xffffffffu, done)) break;
-                ulonglong2 cq[8];
-                const uint4* src4 = reinterpret_cast<const uint4*>(tab + (size_t)n * 2 * C_COUNT);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const uint4 w = GTAB ? __ldg(&src4[q]) : src4[q];
-                    cq[q] = make_ulonglong2(((unsigned long long)w.y << 32) | w.x,
-                                            ((unsigned long long)w.w << 32) | w.z);
+                if (((n - s_begin) & (kExitEvery - 1)) == 0) {
+                    const f2 r2 = fma2(X, X, mul2(Y, Y));
+                    const f2 dot = fma2(X, VX, mul2(Y, VY));
+                    const bool fin0 = !act[0] || (f2lo(r2) >= hc.R2 && f2lo(dot) <= 0.0f);
+                    const bool fin1 = !act[1] || (f2hi(r2) >= hc.R2 && f2hi(dot) <= 0.0f);
+                    done |= fin0 && fin1;
+                    if (__all_sync(0xffffffffu, done)) break;
                 }
-                rk4_step_x2(X, Y, VX, VY, cq, h2);
+                rk4_step_x2<GTAB>(X, Y, VX, VY,
+                                  reinterpret_cast<const uint4*>(tab + (size_t)n * 2 * C_COUNT), h2);
             }
             x[0] = f2lo(X); x[1] = f2hi(X);
             y[0] = f2lo(Y); y[1] = f2hi(Y);
             vx[0] = f2lo(VX); vx[1] = f2hi(VX);
             vy[0] = f2lo(VY); vy[1] = f2hi(VY);
         } else {
-            for (int n = s_begin; n < s_end; ++n) {
-                bool fin = true, fin_i[TPT];
+            bool fin_i[TPT];
 #pragma unroll
-                for (int i = 0; i < TPT; ++i) {
-                    fin_i[i] = !act[i] || (fma(x[i], x[i], y[i] * y[i]) >= hc.R2 &&
-                                           fma(x[i], vx[i], y[i] * vy[i]) <= T(0));
-                    fin &= fin_i[i];
+            for (int i = 0; i < TPT; ++i) fin_i[i] = !act[i];
+            for (int n = s_begin; n < s_end; ++n) {
+                if (((n - s_begin) & (kExitEvery - 1)) == 0) {
+                    bool fin = true;
+#pragma unroll
+                    for (int i = 0; i < TPT; ++i) {
+                        fin_i[i] = !act[i] || (fma(x[i], x[i], y[i] * y[i]) >= hc.R2 &&
+                                               fma(x[i], vx[i], y[i] * vy[i]) <= T(0));
+                        fin &= fin_i[i];
+                    }
+                    done |= fin;
+                    if (__all_sync(0xffffffffu, done)) break;
                 }
-                done |= fin;
-                if (__all_sync(0xffffffffu, done)) break;
                 T c[C_COUNT];
                 const float4* c4 = reinterpret_cast<const float4*>(tab + (size_t)n * C_COUNT);
 #pragma unroll
@@ -644,9 +703,10 @@ __global__ void force_probe_kernel(const DevProblem* __restrict__ prob, int stag
     const int slot = stage >= 2 * P.n_steps ? 2 : (stage & 1);
     const T S = c[(size_t)k * C_COUNT + C_S0 + slot];
     const T Q = c[(size_t)k * C_COUNT + C_Q0 + slot];
+    const T Tq = c[(size_t)k * C_COUNT + C_T0 + slot];
     const typename PrecTraits<T>::Halo hc = PrecTraits<T>::halo(P);
     NoTally none;
-    out[i] = (double)accel_m((T)r[i], T(0), S, Q, hc, none);
+    out[i] = (double)accel_m((T)r[i], T(0), S, Q, Tq, hc, none);
 }
 
 int launch_force_probe(int precision, const DevProblem* d_prob, int stage, const double* d_r, int n,
@@ -709,8 +769,23 @@ int launch_traj(int precision, int tpt, int block, int grid, size_t smem, const 
                 bool gtab)
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (gtab) return launch_shape<true>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
+    if (gtab || smem > kMaxStagedSmem)   // a table too large to stage is read through L1
+        return launch_shape<true>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
     return launch_shape<false>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
+}
+
+template <bool GTAB>
+static int launch_tally_shape(int precision, int tpt, int block, int grid, size_t smem,
+                              const DevProblem* d_probs, const int* d_prefix, int n_probs,
+                              int n_tiles, unsigned* d_counter, unsigned long long* d_tallies,
+                              cudaStream_t s)
+{
+    if (precision == NU_FP64) {
+        if (tpt == 2) return launch_t<double, 2, true, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
+        return launch_t<double, 1, true, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
+    }
+    if (tpt >= 2) return launch_t<float, 2, true, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
+    return launch_t<float, 1, true, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
 }
 
 int launch_traj_tally(int precision, int tpt, int block, int grid, size_t smem,
@@ -718,13 +793,12 @@ int launch_traj_tally(int precision, int tpt, int block, int grid, size_t smem,
                       unsigned* d_counter, unsigned long long* d_tallies, void* stream)
 {
     // the tallies are trajectory facts: every shape integrates the same values
+    // (for a packed batch the scalar two-trajectory kernel counts, bitwise the
+    // same computation; it stages the plain table, which needs less than smem)
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (precision == NU_FP64) {
-        if (tpt == 2) return launch_t<double, 2, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
-        return launch_t<double, 1, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
-    }
-    if (tpt >= 2) return launch_t<float, 2, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
-    return launch_t<float, 1, true>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
+    if (smem > kMaxStagedSmem)
+        return launch_tally_shape<true>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
+    return launch_tally_shape<false>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, s);
 }
 
 template <typename T, int TPT, bool PACKED = false, bool GTAB = false>
@@ -753,7 +827,7 @@ static int occ_shape(int precision, int tpt, int block, size_t smem, int* out)
 
 int max_ctas_per_sm(int precision, int tpt, int block, size_t smem, int* out, bool gtab)
 {
-    return gtab ? occ_shape<true>(precision, tpt, block, smem, out)
+    return (gtab || smem > kMaxStagedSmem) ? occ_shape<true>(precision, tpt, block, smem, out)
                 : occ_shape<false>(precision, tpt, block, smem, out);
 }
 
