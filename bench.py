@@ -61,7 +61,7 @@ SMS, FP32_LANES_PER_SM = 152, 128
 # (dram__bytes_read.sum + dram__bytes_write.sum), recorded in
 # profiles/traj_kernel_precision_sweep_mixed.md.  Must be reset to None
 # whenever the kernel changes, until it is captured again.
-NCU_TRAFFIC_BYTES = {"128x3xg": 688640.0}
+NCU_TRAFFIC_BYTES = {}
 SAMPLE_RADII = (0, 21, 42, 63)
 SAMPLE_MASS_INDEX = 2          # 0.1 eV
 

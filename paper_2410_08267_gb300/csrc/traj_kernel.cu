@@ -150,7 +150,7 @@ __device__ __forceinline__ float accel_m(float x, float y, float S, float Q, flo
     const float r2 = fmaf(x, x, y * y);
     float m = 0.0f;
     if (r2 < hc.R2) {
-        const float rinv = rsqrt_approx(fmaxf(r2, 1e-20f));   // r -> 0 guard (below 1e-10 kpc)
+        const float rinv = rsqrt_approx(r2 + 1e-20f);   // r -> 0 guard (changes r^2 < 2e-13 only)
         const float rs = rinv * S;
         const float ys = r2 * rs;
         if (r2 < Q && ys < 1.0f) {
@@ -374,7 +374,8 @@ __device__ __forceinline__ f2 accel_m_x2(f2 x, f2 y, f2 S, f2 Q, f2 T, const Hal
 {
     const f2 r2 = fma2(x, x, mul2(y, y));
     const float r2a = f2lo(r2), r2b = f2hi(r2);
-    const f2 rinv = pk(rsqrt_approx(fmaxf(r2a, 1e-20f)), rsqrt_approx(fmaxf(r2b, 1e-20f)));
+    const f2 r2g = add2(r2, dup(1e-20f));
+    const f2 rinv = pk(rsqrt_approx(f2lo(r2g)), rsqrt_approx(f2hi(r2g)));
     const f2 rs = mul2(rinv, S);
     const f2 ys = mul2(r2, rs);
     const float ya = f2lo(ys), yb = f2hi(ys);
