@@ -55,7 +55,7 @@ extern "C" {
 #endif
 
 #define NU_VERSION_MAJOR 1
-#define NU_VERSION_MINOR 0
+#define NU_VERSION_MINOR 1
 #define NU_VERSION_PATCH 0
 
 /* ---- error codes ---------------------------------------------------------- */
@@ -125,11 +125,24 @@ typedef struct nu_halo {
     double kappa_p[3];
 } nu_halo;
 
+/* Mass reuse (Sec. III): the equations of motion do not involve the relic
+ * mass, so one set of trajectories serves many masses.  With n_masses = 0 the
+ * request is for the single mass m_eV.  With n_masses >= 1, m_eV is the
+ * fiducial mass that turns the momentum grid into start velocities
+ * (v0 = c q k_B T0 / m_eV), and each of masses_eV[0 .. n_masses-1] reads the
+ * same trajectories with momenta P = m v: for mass m_a the momentum nodes and
+ * the final momenta are those of the fiducial mass times s_a = m_a / m_eV,
+ * and the trapezoid weights in ln q are unchanged, so
+ *   n/nbar_a = sum_jk w_j q_j^3 w_k f(s_a q_i) / (2 sum_j w_j q_j^3 f(s_a q_j)).
+ * Results are then [n_masses][n_radii].  masses_eV is borrowed for the call. */
+#define NU_MAX_MASSES 64
+
 typedef struct nu_relic {
-    double m_eV;     /* relic mass, eV (> 0)                                   */
+    double m_eV;     /* relic mass, eV (> 0); the fiducial mass if n_masses > 0 */
     int f_kind;      /* NU_F_*                                                 */
-    int reserved;
+    int n_masses;    /* 0: one mass m_eV; 1 .. NU_MAX_MASSES: masses_eV        */
     double f_p[2];
+    const double* masses_eV;   /* [n_masses] relic masses, eV (> 0)            */
 } nu_relic;
 
 typedef struct nu_pgrid {
@@ -187,6 +200,8 @@ typedef struct nu_plan_info {
     int tile;                /* trajectories per tile (block * tpt)           */
     int precision;           /* NU_FP64 or NU_MIXED                           */
     int n_steps;             /* RK4 steps                                     */
+    int n_masses;            /* masses read from the trajectories (>= 1)      */
+    int reserved;
 } nu_plan_info;
 
 /* Fill *info for the request (validation + Sec. II.B derivation + sizing).
@@ -217,8 +232,10 @@ NU_API int nu_profile_run(nu_profile* h, void* stream);
 /* Wait for the last run of `h` and copy n/nbar (and, if err_est != NULL, an
  * estimate of the relative quadrature error of each value: the difference to
  * the same sum on a grid with every other q node, divided by 3) into host
- * arrays of n_radii doubles.  Errors: NU_EBUSY (never run), NU_EINVAL
- * (n_radii mismatch), NU_EDEVICE (non-finite sum), NU_ECUDA. */
+ * arrays of n_radii doubles.  For a request with several masses (nu_relic
+ * n_masses > 0) the arrays hold [n_masses][n_radii] values and n_radii must be
+ * n_masses times the number of radii.  Errors: NU_EBUSY (never run), NU_EINVAL
+ * (size mismatch), NU_EDEVICE (non-finite sum), NU_ECUDA. */
 NU_API int nu_profile_result(nu_profile* h, double* n_over_nbar, double* err_est, int n_radii);
 
 /* Copy the final momenta q_i (units of k_B T0) of every trajectory of the last
@@ -362,7 +379,9 @@ NU_API int nu_server_submit(nu_server* s, const nu_cosmo* cosmo, const nu_halo* 
 /* NU_EAGAIN while the request runs; when it is done, copies n/nbar, the error
  * estimate (may be NULL) and the submit-to-result latency (may be NULL) and
  * returns the request's status (NU_OK, NU_ECANCELED, NU_ENOMEM, NU_ETIMEDOUT ...)
- * once; NU_EINVAL for an unknown or already delivered ticket or a wrong n_radii. */
+ * once; NU_EINVAL for an unknown or already delivered ticket or a wrong n_radii
+ * (for a mass-reuse request, n_masses times its number of radii; the server
+ * keeps its own copy of the mass list). */
 NU_API int nu_server_poll(nu_server* s, long long ticket, double* n_over_nbar, double* err_est,
                           int n_radii, double* latency_ms);
 /* Cancel a queued or running request (it completes with NU_ECANCELED before
@@ -398,9 +417,10 @@ NU_API void nu_server_destroy(nu_server* s);
  *   never overlap; any other work that touched the array while a call ran
  *   would race with it.  The array keeps the last call's contents; each call
  *   clears the counters that must start at zero.
- *   Errors: NU_EINVAL, NU_ENOTSUP, NU_ETOOBIG (the request needs more than
- *   NU_NOALLOC_MAX_BYTES, e.g. too many radii x tiles or steps), NU_EDEVICE,
- *   NU_ECUDA. */
+ *   Errors: NU_EINVAL, NU_ENOTSUP (the packed shape tpt = 3, or a mass-reuse
+ *   relic: this entry point computes one mass), NU_ETOOBIG (the request needs
+ *   more than NU_NOALLOC_MAX_BYTES, e.g. too many radii x tiles or steps),
+ *   NU_EDEVICE, NU_ECUDA. */
 NU_API int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* halo,
                                       const nu_relic* relic, const double* radii, int n_radii,
                                       const nu_pgrid* p_grid, const nu_opts* opts,

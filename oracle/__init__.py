@@ -81,6 +81,10 @@ def lib():
                                            C.c_double, C.c_int, C.c_double, C.c_ulonglong, C.c_int,
                                            dp, dp]
         L.or_profile_perturbed.restype = C.c_int
+        L.or_profile_masses.argtypes = [P, dp, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int,
+                                        C.c_int, C.c_double, C.c_double, C.c_int,
+                                        C.c_int, C.c_double, C.c_int, dp, C.c_int, dp]
+        L.or_profile_masses.restype = C.c_int
         L.or_initial_state.argtypes = [P, C.c_double, C.c_double, C.c_double, dp]
         L.or_initial_state.restype = None
         L.or_final_q.argtypes = [P, dp]
@@ -248,3 +252,26 @@ def profile_perturbed(pb, eps: float, seed: int, radius_sel=None, n_threads: int
     if rc != 0:
         raise ValueError(f"oracle rejected the problem (rc={rc})")
     return (out, qi) if return_qi else out
+
+
+def profile_masses(pb, masses, radius_sel=None, n_threads: int = 0):
+    """Sec. III mass reuse: trajectories of the fiducial pb.m_eV read for every
+    mass in ``masses``; returns an array [len(masses), n_radii] (NaN where not
+    computed)."""
+    p = params(pb)
+    radii = np.ascontiguousarray(np.asarray(pb.radii, dtype=np.float64))
+    m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64))
+    n_r = len(radii)
+    out = np.full((len(m), n_r), np.nan)
+    if radius_sel is None:
+        sel_ptr, n_sel = None, n_r
+    else:
+        sel = np.ascontiguousarray(np.asarray(radius_sel, dtype=np.int32))
+        sel_ptr, n_sel = sel.ctypes.data_as(C.POINTER(C.c_int)), len(sel)
+    rc = lib().or_profile_masses(C.byref(p), _dptr(radii), n_r, int(pb.radii_unit), sel_ptr, n_sel,
+                                 int(pb.n_q), float(pb.q_min), float(pb.q_max), int(pb.n_mu),
+                                 int(pb.n_steps), float(pb.z_end), int(n_threads), _dptr(m), len(m),
+                                 _dptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the problem (rc={rc})")
+    return out

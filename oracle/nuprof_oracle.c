@@ -469,6 +469,84 @@ done:
     return rc;
 }
 
+/* Sec. III (numerical methods): the equations of motion do not contain the
+ * relic mass, so the trajectories are solved once, for the fiducial mass
+ * p->m_eV, and read for every mass of a list.  A trajectory started with
+ * momentum q_j (units of k_B T0) of the fiducial mass has the velocity of a
+ * particle of mass m_a started with momentum s_a q_j, s_a = m_a / m_eV, and
+ * ends with momentum s_a q_i.  The momentum grid of mass m_a is therefore the
+ * fiducial grid times s_a, with the same trapezoid weights in ln q, and
+ *   n/nbar_a = sum_jk w_j (s_a q_j)^3 w_k f(s_a q_i) / (2 sum_j w_j (s_a q_j)^3 f(s_a q_j)).
+ * out holds [n_masses][n_radii] values (NaN-free only where computed). */
+int or_profile_masses(const or_params* p, const double* radii, int n_radii, int radii_unit,
+                      const int* radius_sel, int n_sel,
+                      int n_q, double q_min, double q_max, int n_mu,
+                      int nsteps, double z_end, int n_threads,
+                      const double* masses, int n_masses, double* out)
+{
+    or_derived d;
+    if (or_derive(p, &d) != 0) return -1;
+    if (z_end <= 0.0) z_end = d.z_i;
+    if (n_radii < 1 || n_mu < 1 || nsteps < 1 || n_masses < 1 || !(z_end > p->z0) ||
+        !(p->m_eV > 0.0))
+        return -1;
+    for (int a = 0; a < n_masses; ++a)
+        if (!(masses[a] > 0.0)) return -1;
+    long ntr = (long)n_q * n_mu;
+    double* q = (double*)malloc(sizeof(double) * (size_t)n_q);
+    double* wl = (double*)malloc(sizeof(double) * (size_t)n_q);
+    double* mu = (double*)malloc(sizeof(double) * (size_t)n_mu);
+    double* wmu = (double*)malloc(sizeof(double) * (size_t)n_mu);
+    double* qi = (double*)malloc(sizeof(double) * (size_t)ntr);
+    double* contrib = (double*)malloc(sizeof(double) * (size_t)ntr);
+    double* bg = (double*)malloc(sizeof(double) * (size_t)n_q);
+    int rc = 0;
+    if (!q || !wl || !mu || !wmu || !qi || !contrib || !bg) { rc = -2; goto done; }
+    if (or_log_grid(n_q, q_min, q_max, q, wl) != 0) { rc = -1; goto done; }
+    if (or_gauss_legendre(n_mu, mu, wmu) != 0) { rc = -1; goto done; }
+    double u_end = -log1p(z_end);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    int nsel = radius_sel ? n_sel : n_radii;
+    for (int si = 0; si < nsel; ++si) {
+        int ir = radius_sel ? radius_sel[si] : si;
+        if (ir < 0 || ir >= n_radii) { rc = -1; goto done; }
+        double x0 = (radii_unit == 1) ? radii[ir] * d.r200 : radii[ir];
+        if (!(x0 > 0.0)) { rc = -1; goto done; }
+        /* the trajectories of the fiducial mass */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+        for (long t = 0; t < ntr; ++t) {
+            int j = (int)(t / n_mu), k = (int)(t % n_mu);
+            double st[4];
+            or_initial_state(p, x0, q[j], mu[k], st);
+            or_integrate(p, &d, st, 0.0, u_end, nsteps);
+            qi[t] = or_final_q(p, st);
+        }
+        /* every mass reads them with momenta scaled by s_a */
+        for (int a = 0; a < n_masses; ++a) {
+            double sa = masses[a] / p->m_eV;
+            for (int j = 0; j < n_q; ++j) {
+                double qa = sa * q[j];
+                bg[j] = wl[j] * qa * qa * qa * or_f(p, qa);
+            }
+            for (long t = 0; t < ntr; ++t) {
+                int j = (int)(t / n_mu), k = (int)(t % n_mu);
+                double qa = sa * q[j];
+                contrib[t] = wl[j] * qa * qa * qa * wmu[k] * or_f(p, sa * qi[t]);
+            }
+            out[(long)a * n_radii + ir] = csum(contrib, ntr) / (2.0 * csum(bg, n_q));
+        }
+    }
+done:
+    free(q); free(wl); free(mu); free(wmu); free(qi); free(contrib); free(bg);
+    return rc;
+}
+
 /* Number of OpenMP threads the oracle would use (1 without OpenMP). */
 int or_max_threads(void)
 {

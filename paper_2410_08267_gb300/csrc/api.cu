@@ -167,13 +167,14 @@ int plan_common(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* reli
     const int tps_alloc = (int)((seg + kMinTile - 1) / kMinTile);
     info.device_bytes = device_bytes(o.precision, o.n_steps, n_radii, grid->n_q, grid->n_mu,
                                      tps_alloc, (o.flags & NU_FLAG_KEEP_QI) != 0,
-                                     &info.h2d_bytes);
+                                     relic_n_mass(*relic), &info.h2d_bytes);
     const long long nt = (long long)tiles_per_seg * n_radii;
     if (nt > (1LL << 30)) return NU_EINVAL;
     info.n_tiles = (int)nt;
     info.tile = tile;
     info.precision = o.precision;
     info.n_steps = o.n_steps;
+    info.n_masses = relic_n_mass(*relic);
     return NU_OK;
 }
 
@@ -191,6 +192,7 @@ namespace nuprof {
 
 const DevProblem& profile_desc(const nu_profile* h) { return h->hdp; }
 int profile_n_radii(const nu_profile* h) { return h->n_radii; }
+int profile_n_out(const nu_profile* h) { return h->n_radii * h->hdp.n_mass; }
 int profile_n_steps(const nu_profile* h) { return h->opts.n_steps; }
 long long profile_n_traj(const nu_profile* h) { return h->info.n_traj; }
 
@@ -199,14 +201,15 @@ long long profile_n_traj(const nu_profile* h) { return h->info.n_traj; }
 int profile_read(const nu_profile* h, double* out, double* err, void* stream)
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const size_t bytes = (size_t)h->n_radii * sizeof(double);
+    const int n = profile_n_out(h);
+    const size_t bytes = (size_t)n * sizeof(double);
     if (cudaMemcpyAsync(out, h->hdp.out, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         (err && cudaMemcpyAsync(err, h->hdp.err, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return NU_ECUDA;
     }
-    for (int i = 0; i < h->n_radii; ++i)
+    for (int i = 0; i < n; ++i)
         if (!std::isfinite(out[i])) return NU_EDEVICE;
     return NU_OK;
 }
@@ -269,6 +272,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     h->cosmo = *cosmo;
     h->halo = *halo;
     h->relic = *relic;
+    h->relic.masses_eV = nullptr;                         // borrowed: not kept
     h->grid = *p_grid;
     h->opts = o;
     h->d = d;
@@ -290,11 +294,20 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     for (int k = 0; k < nmu; ++k) smu[k] = std::sqrt((1.0 - mu[k]) * (1.0 + mu[k]));
     for (int i = 0; i < n_radii; ++i)
         x0[i] = o.radii_unit == NU_RADII_R200 ? radii[i] * d.r200 : radii[i];
-    double nb = 0.0, nbc = 0.0;                            // background, same grid
-    for (int j = 0; j < nq; ++j) {
-        const double f = relic_f(*relic, q[j]);
-        nb += wq[j] * f;
-        nbc += wqc[j] * f;
+    // Masses read from the trajectories (Sec. III): scale s_a = m_a / m and the
+    // background of each on the same (scaled) grid.
+    const int nm = relic_n_mass(*relic);
+    std::vector<double> mass_s(nm), norms(2 * (size_t)nm);
+    for (int a = 0; a < nm; ++a) {
+        mass_s[a] = relic->n_masses > 0 ? relic->masses_eV[a] / relic->m_eV : 1.0;
+        double nb = 0.0, nbc = 0.0;
+        for (int j = 0; j < nq; ++j) {
+            const double f = relic_f(*relic, mass_s[a] * q[j]);
+            nb += wq[j] * f;
+            nbc += wqc[j] * f;
+        }
+        norms[2 * a] = 1.0 / (2.0 * nb);
+        norms[2 * a + 1] = 1.0 / (2.0 * nbc);
     }
 
     // ---- device layout ----
@@ -314,13 +327,14 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     const size_t o_wq = carve((size_t)nq * sizeof(double));
     const size_t o_wqc = carve((size_t)nq * sizeof(double));
     const size_t o_wmu = carve((size_t)nmu * sizeof(double));
+    const size_t o_mass = carve((size_t)nm * 3 * sizeof(double));   // scales, then norms
     const size_t upload_end = off;                         // everything above is uploaded
     // tile sums sized for the smallest tile shape, so that any batch shape fits
     const size_t tps_alloc = (size_t)(((long long)nq * nmu + kMinTile - 1) / kMinTile);
-    const size_t o_part = carve((size_t)n_radii * tps_alloc * 2 * sizeof(double));
+    const size_t o_part = carve((size_t)n_radii * tps_alloc * 2 * nm * sizeof(double));
     const size_t o_cnt = carve((size_t)n_radii * sizeof(unsigned));
-    const size_t o_out = carve((size_t)n_radii * sizeof(double));
-    const size_t o_err = carve((size_t)n_radii * sizeof(double));
+    const size_t o_out = carve((size_t)n_radii * nm * sizeof(double));
+    const size_t o_err = carve((size_t)n_radii * nm * sizeof(double));
     const bool keep_qi = (o.flags & NU_FLAG_KEEP_QI) != 0;
     const size_t o_qi = keep_qi ? carve((size_t)n_radii * nq * nmu * sz) : 0;
     const size_t total = off;
@@ -340,6 +354,8 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     P.wq = reinterpret_cast<const double*>(base + o_wq);
     P.wqc = reinterpret_cast<const double*>(base + o_wqc);
     P.wmu = reinterpret_cast<const double*>(base + o_wmu);
+    P.mass_s = reinterpret_cast<const double*>(base + o_mass);
+    P.norms = reinterpret_cast<const double*>(base + o_mass) + nm;
     P.partials = reinterpret_cast<double*>(base + o_part);
     P.seg_count = reinterpret_cast<unsigned*>(base + o_cnt);
     P.out = reinterpret_cast<double*>(base + o_out);
@@ -347,8 +363,6 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     P.qi = keep_qi ? static_cast<void*>(base + o_qi) : nullptr;
     P.status = reinterpret_cast<int*>(base + o_ctrl + sizeof(unsigned));
     P.q_scale = relic->m_eV / (kC * kT0);                 // Liouville map: q_i = m |v| / (c k_B T0)
-    P.inv_norm = 1.0 / (2.0 * nb);
-    P.inv_norm_c = 1.0 / (2.0 * nbc);
     P.invIc = 1.0 / d.Ic;
     P.invR3 = d.R > 0.0 ? 1.0 / (d.R * d.R * d.R) : 0.0;
     P.R2 = d.R * d.R;
@@ -361,6 +375,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     P.tiles_per_seg = tps;
     P.tile = o.block * traj_per_thread(o.tpt);
     P.precision = o.precision;
+    P.n_mass = nm;
 
     std::vector<unsigned char> stage(upload_end, 0);
     std::memcpy(stage.data() + o_prob, &P, sizeof(P));
@@ -384,6 +399,8 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     put<double>(stage, o_wq, wq.data(), nq);
     put<double>(stage, o_wqc, wqc.data(), nq);
     put<double>(stage, o_wmu, wmu.data(), nmu);
+    put<double>(stage, o_mass, mass_s.data(), nm);
+    put<double>(stage, o_mass + nm * sizeof(double), norms.data(), 2 * (size_t)nm);
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
     if (cudaMemcpyAsync(base, stage.data(), upload_end, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -426,7 +443,7 @@ int nu_profile_run(nu_profile* h, void* stream)
 int nu_profile_result(nu_profile* h, double* n_over_nbar, double* err_est, int n_radii)
 {
     if (!h || !n_over_nbar) return NU_EINVAL;
-    if (n_radii != h->n_radii) return NU_EINVAL;
+    if (n_radii != profile_n_out(h)) return NU_EINVAL;
     if (!h->last) return NU_EBUSY;
     if (cudaEventSynchronize(h->last->ev) != cudaSuccess) {
         cudaGetLastError();

@@ -37,6 +37,12 @@ int validate(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
     }
     if (!(relic->m_eV > 0.0) || !std::isfinite(relic->m_eV)) return NU_EINVAL;
     if (relic->f_kind < NU_F_FD || relic->f_kind > NU_F_FREEZEIN) return NU_EINVAL;
+    if (relic->n_masses < 0 || relic->n_masses > NU_MAX_MASSES) return NU_EINVAL;
+    if (relic->n_masses > 0) {                        // mass reuse (Sec. III)
+        if (!relic->masses_eV) return NU_EINVAL;
+        for (int a = 0; a < relic->n_masses; ++a)
+            if (!(relic->masses_eV[a] > 0.0) || !std::isfinite(relic->masses_eV[a])) return NU_EINVAL;
+    }
     if (n_radii < 1) return NU_EINVAL;
     for (int i = 0; i < n_radii; ++i)
         if (!(radii[i] > 0.0) || !std::isfinite(radii[i])) return NU_EINVAL;
@@ -278,7 +284,7 @@ static void gauss_legendre_compute(int n, std::vector<double>& x, std::vector<do
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_mu,
-                       int tiles_per_seg, bool keep_qi, long long* h2d_bytes)
+                       int tiles_per_seg, bool keep_qi, int n_mass, long long* h2d_bytes)
 {
     const size_t sz = precision == NU_FP64 ? sizeof(double) : sizeof(float);
     size_t b = 0;
@@ -292,10 +298,11 @@ long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_m
     b += 2 * align256((size_t)n_mu * sz);                        // mu, sin psi
     b += 2 * align256((size_t)n_q * sizeof(double));             // wq, wqc
     b += align256((size_t)n_mu * sizeof(double));                // wmu
+    b += align256((size_t)n_mass * 3 * sizeof(double));          // mass scales, normalisations
     if (h2d_bytes) *h2d_bytes = (long long)b;                    // everything above is uploaded
-    b += align256((size_t)n_radii * tiles_per_seg * 2 * sizeof(double));
+    b += align256((size_t)n_radii * tiles_per_seg * 2 * n_mass * sizeof(double));
     b += align256((size_t)n_radii * sizeof(unsigned));
-    b += 2 * align256((size_t)n_radii * sizeof(double));         // out, err
+    b += 2 * align256((size_t)n_radii * n_mass * sizeof(double));   // out, err
     if (keep_qi) b += align256((size_t)n_radii * n_q * n_mu * sz);
     return (long long)b;
 }

@@ -70,7 +70,9 @@ void log_nodes(int n, double q_min, double q_max, std::vector<double>& q,
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 void resolve_opts(const nu_opts* in, nu_opts& out);
 long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_mu,
-                       int tiles_per_seg, bool keep_qi, long long* h2d_bytes);
+                       int tiles_per_seg, bool keep_qi, int n_mass, long long* h2d_bytes);
+// Number of masses read from one trajectory set (Sec. III mass reuse).
+inline int relic_n_mass(const nu_relic& r) { return r.n_masses > 0 ? r.n_masses : 1; }
 
 // Device-visible description of one request (POD, lives in device memory).
 struct DevProblem {
@@ -83,21 +85,22 @@ struct DevProblem {
     const double* wq;       // [n_q] trapezoid-in-ln q weight x q^3
     const double* wqc;      // [n_q] same on every other node (error estimate)
     const double* wmu;      // [n_mu] Gauss-Legendre weights
-    double* partials;       // [n_radii][tiles_per_seg][2] tile sums
+    const double* mass_s;   // [n_mass] mass scale s_a = m_a / m (1 for one mass)
+    const double* norms;    // [n_mass][2] 1/(2 sum_j wq_j f(s_a q_j)), same with wqc
+    double* partials;       // [n_radii][tiles_per_seg][n_mass][2] tile sums
     unsigned* seg_count;    // [n_radii] tiles finished (reset by the finisher)
-    double* out;            // [n_radii] n/nbar
-    double* err;            // [n_radii] relative quadrature-error estimate
+    double* out;            // [n_mass][n_radii] n/nbar
+    double* err;            // [n_mass][n_radii] relative quadrature-error estimate
     void* qi;               // [n_radii][n_q][n_mu] final q in the state precision (optional)
     int* status;            // bit 0: non-finite sum
-    double q_scale;         // q_i = |v| * q_scale
-    double inv_norm;        // 1 / (2 sum_j wq_j f(q_j))
-    double inv_norm_c;      // same with wqc
+    double q_scale;         // q_i = |v| * q_scale (fiducial mass)
     double invIc, invR3, R2;
     double f_p0;
     int f_kind;
     int n_radii, n_q, n_mu, n_steps;
     int tiles_per_seg, tile;
     int precision;
+    int n_mass;
     // Chunked integration (serving): when `state` is set, a launch advances
     // steps [step_begin, step_end) and keeps each trajectory's (x, y, vx, vy)
     // in `state` ([n_radii][n_q][n_mu] of 4 values in the state precision);
@@ -110,6 +113,7 @@ struct DevProblem {
 // Accessors used by the request server (api.cu).
 const DevProblem& profile_desc(const nu_profile* h);
 int profile_n_radii(const nu_profile* h);
+int profile_n_out(const nu_profile* h);   // n_mass * n_radii result values
 int profile_n_steps(const nu_profile* h);
 long long profile_n_traj(const nu_profile* h);
 int profile_read(const nu_profile* h, double* out, double* err, void* stream);

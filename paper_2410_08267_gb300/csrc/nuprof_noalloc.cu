@@ -194,6 +194,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     resolve_opts(opts, o);
     if (o.flags != 0) return NU_EINVAL;
     if (o.tpt == kTptPacked) return NU_ENOTSUP;   // the packed table is not staged here
+    if (relic && relic->n_masses > 0) return NU_ENOTSUP;   // one mass per call
     int rc = validate(cosmo, halo, relic, radii, n_radii, p_grid, &o);
     if (rc != NU_OK) return rc;
     Derived d;
@@ -224,6 +225,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     const size_t o_wq = carve((size_t)nq * sizeof(double));
     const size_t o_wqc = carve((size_t)nq * sizeof(double));
     const size_t o_wmu = carve((size_t)nmu * sizeof(double));
+    const size_t o_mass = carve(3 * sizeof(double));      // mass scale 1, two normalisations
     const size_t upload_end = off;
     const size_t o_part = carve((size_t)n_radii * tps * 2 * sizeof(double));
     const size_t o_cnt = carve((size_t)n_radii * sizeof(unsigned));
@@ -279,6 +281,8 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     P.wq = reinterpret_cast<const double*>(dev + o_wq);
     P.wqc = reinterpret_cast<const double*>(dev + o_wqc);
     P.wmu = reinterpret_cast<const double*>(dev + o_wmu);
+    P.mass_s = reinterpret_cast<const double*>(dev + o_mass);
+    P.norms = reinterpret_cast<const double*>(dev + o_mass) + 1;
     P.partials = reinterpret_cast<double*>(dev + o_part);
     P.seg_count = reinterpret_cast<unsigned*>(dev + o_cnt);
     P.out = reinterpret_cast<double*>(dev + o_out);
@@ -286,8 +290,6 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     P.qi = nullptr;
     P.status = reinterpret_cast<int*>(dev + o_ctrl + sizeof(unsigned));
     P.q_scale = relic->m_eV / (kC * kT0);
-    P.inv_norm = 1.0 / (2.0 * nb);
-    P.inv_norm_c = 1.0 / (2.0 * nbc);
     P.invIc = 1.0 / d.Ic;
     P.invR3 = d.R > 0.0 ? 1.0 / (d.R * d.R * d.R) : 0.0;
     P.R2 = d.R * d.R;
@@ -300,6 +302,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     P.tiles_per_seg = tps;
     P.tile = tile;
     P.precision = o.precision;
+    P.n_mass = 1;
 
     // ---- uploaded image: control words (zero), descriptor, prefix, tables ----
     std::memcpy(st + o_prob, &P, sizeof(P));
@@ -321,6 +324,8 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     put_into<double>(st, o_wq, wq, nq);
     put_into<double>(st, o_wqc, wqc, nq);
     put_into<double>(st, o_wmu, wmu, nmu);
+    const double mass[3] = {1.0, 1.0 / (2.0 * nb), 1.0 / (2.0 * nbc)};
+    put_into<double>(st, o_mass, mass, 3);
 
     int per_sm = 0, sms = 0, devid = 0;
     const size_t smem = coef_smem_bytes(o.precision, N, o.tpt);

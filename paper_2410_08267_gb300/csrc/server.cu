@@ -119,7 +119,9 @@ struct Pending {
     nu_pgrid grid;
     nu_opts opts;
     std::vector<double> radii;
+    std::vector<double> masses;   // relic masses of a mass-reuse request (owned copy)
     Clock::time_point t_submit;
+    void fix() { relic.masses_eV = masses.empty() ? nullptr : masses.data(); }
 };
 
 struct Active {
@@ -225,6 +227,7 @@ bool nu_server::admit_one()
         }
         p = pending.front();
     }
+    p.fix();
     nu_plan_info info;
     int rc = nu_profile_plan(&p.cosmo, &p.halo, &p.relic, p.radii.data(), (int)p.radii.size(),
                              &p.grid, &p.opts, &info);
@@ -408,7 +411,7 @@ void nu_server::run()
                 keep.push_back(a);
                 continue;
             }
-            const int nr = profile_n_radii(a.h);
+            const int nr = profile_n_out(a.h);
             std::vector<double> out(nr), err(nr);
             const int r = profile_read(a.h, out.data(), err.data(), upload);
             finish(a, r, &out, &err);
@@ -508,6 +511,9 @@ int nu_server_submit(nu_server* s, const nu_cosmo* cosmo, const nu_halo* halo, c
     p.opts.alloc_ctx = &s->arena;
     p.opts.stream = s->upload;
     p.radii.assign(radii, radii + n_radii);
+    if (relic->n_masses > 0 && relic->masses_eV)
+        p.masses.assign(relic->masses_eV, relic->masses_eV + std::min(relic->n_masses, NU_MAX_MASSES));
+    p.fix();
     nu_plan_info info;
     const int rc = nu_profile_plan(&p.cosmo, &p.halo, &p.relic, radii, n_radii, &p.grid, &p.opts, &info);
     if (rc != NU_OK) return rc;

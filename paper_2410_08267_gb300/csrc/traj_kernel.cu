@@ -616,65 +616,79 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             continue;
         }
 
-        // Liouville map and the weight of each trajectory in Eq. localdensity
-        double acc = 0.0, accc = 0.0;
+        // Liouville map and the weight of each trajectory in Eq. localdensity.
+        // The final momentum is that of the fiducial mass; mass a of a
+        // mass-reuse request reads it scaled by s_a (Sec. III).
+        T qf[TPT];
 #pragma unroll
         for (int i = 0; i < TPT; ++i) {
-            if (!act[i]) continue;
             const T vmag = sqrt(vx[i] * vx[i] + vy[i] * vy[i]);
-            const T qi = vmag * (T)P.q_scale;
-            const double f = (double)relic_f_dev(P.f_kind, (T)P.f_p0, qi);
-            const double wm = P.wmu[tk[i]];
-            acc += P.wq[tj[i]] * wm * f;
-            accc += P.wqc[tj[i]] * wm * f;
-            if (P.qi) {
+            qf[i] = vmag * (T)P.q_scale;
+            if (P.qi && act[i]) {
                 const int t = tis * P.tile + i * blockDim.x + threadIdx.x;
-                reinterpret_cast<T*>(P.qi)[(size_t)seg * n_seg + t] = qi;
+                reinterpret_cast<T*>(P.qi)[(size_t)seg * n_seg + t] = qf[i];
             }
         }
-
-        // tile sum: warp shuffle, then the warps in order
-        acc = warp_sum(acc);
-        accc = warp_sum(accc);
-        if (lane == 0) {
-            s_red[warp][0] = acc;
-            s_red[warp][1] = accc;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            double a = lane < nwarps ? s_red[lane][0] : 0.0;
-            double ac = lane < nwarps ? s_red[lane][1] : 0.0;
-            a = warp_sum(a);
-            ac = warp_sum(ac);
+        const int nm = P.n_mass;
+        double* part = P.partials + ((size_t)seg * tps + tis) * 2 * nm;
+        for (int a = 0; a < nm; ++a) {
+            const T sa = (T)P.mass_s[a];
+            double acc = 0.0, accc = 0.0;
+#pragma unroll
+            for (int i = 0; i < TPT; ++i) {
+                if (!act[i]) continue;
+                const double f = (double)relic_f_dev(P.f_kind, (T)P.f_p0, qf[i] * sa);
+                const double wm = P.wmu[tk[i]];
+                acc += P.wq[tj[i]] * wm * f;
+                accc += P.wqc[tj[i]] * wm * f;
+            }
+            // tile sum: warp shuffle, then the warps in order
+            acc = warp_sum(acc);
+            accc = warp_sum(accc);
             if (lane == 0) {
-                double* part = P.partials + ((size_t)seg * tps + tis) * 2;
-                part[0] = a;
-                part[1] = ac;
-                __threadfence();
-                const unsigned prev = atomicAdd(&P.seg_count[seg], 1u);
-                s_last = (prev == (unsigned)(tps - 1));
+                s_red[warp][0] = acc;
+                s_red[warp][1] = accc;
             }
+            __syncthreads();
+            if (warp == 0) {
+                double t0 = lane < nwarps ? s_red[lane][0] : 0.0;
+                double t1 = lane < nwarps ? s_red[lane][1] : 0.0;
+                t0 = warp_sum(t0);
+                t1 = warp_sum(t1);
+                if (lane == 0) {
+                    part[2 * a] = t0;
+                    part[2 * a + 1] = t1;
+                }
+            }
+            __syncthreads();   // s_red is reused by the next mass
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&P.seg_count[seg], 1u);
+            s_last = (prev == (unsigned)(tps - 1));
         }
         __syncthreads();
 
         if (s_last && warp == 0) {   // this CTA finished the radius: add tiles in order
             __threadfence();
-            const double* part = P.partials + (size_t)seg * tps * 2;
-            double a = 0.0, ac = 0.0;
-            for (int i = lane; i < tps; i += 32) {
-                a += __ldcg(&part[2 * i]);
-                ac += __ldcg(&part[2 * i + 1]);
+            const double* sp = P.partials + (size_t)seg * tps * 2 * nm;
+            for (int a = 0; a < nm; ++a) {
+                double t0 = 0.0, t1 = 0.0;
+                for (int i = lane; i < tps; i += 32) {
+                    t0 += __ldcg(&sp[(size_t)i * 2 * nm + 2 * a]);
+                    t1 += __ldcg(&sp[(size_t)i * 2 * nm + 2 * a + 1]);
+                }
+                t0 = warp_sum(t0);
+                t1 = warp_sum(t1);
+                if (lane == 0) {
+                    const double ratio = t0 * P.norms[2 * a];
+                    const double ratio_c = t1 * P.norms[2 * a + 1];
+                    P.out[(size_t)a * P.n_radii + seg] = ratio;
+                    P.err[(size_t)a * P.n_radii + seg] = fabs(ratio - ratio_c) / (3.0 * fabs(ratio));
+                    if (!isfinite(ratio)) atomicOr(P.status, 1);
+                }
             }
-            a = warp_sum(a);
-            ac = warp_sum(ac);
-            if (lane == 0) {
-                const double ratio = a * P.inv_norm;
-                const double ratio_c = ac * P.inv_norm_c;
-                P.out[seg] = ratio;
-                P.err[seg] = fabs(ratio - ratio_c) / (3.0 * fabs(ratio));
-                if (!isfinite(ratio)) atomicOr(P.status, 1);
-                P.seg_count[seg] = 0u;   // ready for the next run
-            }
+            if (lane == 0) P.seg_count[seg] = 0u;   // ready for the next run
         }
         // the next iteration's first __syncthreads orders s_tile/s_last reuse
     }

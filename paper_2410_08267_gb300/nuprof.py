@@ -27,6 +27,7 @@ NU_FP64, NU_MIXED = 0, 1
 NU_RADII_KPC, NU_RADII_R200 = 0, 1
 NU_FLAG_KEEP_QI, NU_FLAG_GRAPH, NU_FLAG_TIMING, NU_FLAG_GTAB = 1, 2, 4, 8
 NU_MAX_STEPS = 3000
+NU_MAX_MASSES = 64
 
 
 class NuError(RuntimeError):
@@ -46,8 +47,8 @@ class nu_halo(C.Structure):
 
 
 class nu_relic(C.Structure):
-    _fields_ = [("m_eV", C.c_double), ("f_kind", C.c_int), ("reserved", C.c_int),
-                ("f_p", C.c_double * 2)]
+    _fields_ = [("m_eV", C.c_double), ("f_kind", C.c_int), ("n_masses", C.c_int),
+                ("f_p", C.c_double * 2), ("masses_eV", C.POINTER(C.c_double))]
 
 
 class nu_pgrid(C.Structure):
@@ -71,7 +72,8 @@ class nu_plan_info(C.Structure):
                 ("z_end", C.c_double), ("n_traj", C.c_longlong), ("h2d_bytes", C.c_longlong),
                 ("traj_steps", C.c_longlong),
                 ("device_bytes", C.c_longlong), ("n_tiles", C.c_int), ("tile", C.c_int),
-                ("precision", C.c_int), ("n_steps", C.c_int)]
+                ("precision", C.c_int), ("n_steps", C.c_int), ("n_masses", C.c_int),
+                ("reserved", C.c_int)]
 
 
 class nu_server_opts(C.Structure):
@@ -222,6 +224,10 @@ def structs(pb: "W.Problem", block: int = 0, tpt: int = 0, flags: int = 0, strea
     relic = nu_relic()
     relic.m_eV, relic.f_kind = pb.m_eV, int(pb.f_kind)
     relic.f_p[0], relic.f_p[1] = float(pb.f_p[0]), float(pb.f_p[1])
+    if len(pb.masses):                      # mass reuse: m_eV is the fiducial mass
+        relic._masses = np.ascontiguousarray(np.asarray(pb.masses, dtype=np.float64))
+        relic.n_masses = len(relic._masses)
+        relic.masses_eV = relic._masses.ctypes.data_as(C.POINTER(C.c_double))
     grid = nu_pgrid(int(pb.n_q), int(pb.n_mu), float(pb.q_min), float(pb.q_max))
     opts = nu_opts()
     opts.n_steps, opts.precision, opts.z_end = int(pb.n_steps), int(pb.precision), float(pb.z_end)
@@ -444,6 +450,6 @@ def profile(pb: "W.Problem", stream=None, **kw):
     h = create(pb, stream=stream, **kw)
     try:
         nu_profile_run(h, stream)
-        return nu_profile_result(h, pb.n_radii)
+        return nu_profile_result(h, pb.n_out)
     finally:
         nu_profile_destroy(h)

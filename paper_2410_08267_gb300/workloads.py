@@ -57,10 +57,17 @@ class Problem:
     n_steps: int = 400
     z_end: float = 4.0
     precision: int = MIXED
+    masses: tuple = ()                     # mass reuse: relic masses read from the
+                                           # trajectories of the fiducial m_eV
 
     @property
     def n_radii(self) -> int:
         return int(len(self.radii))
+
+    @property
+    def n_out(self) -> int:
+        """Result values: radii x masses."""
+        return self.n_radii * max(1, len(self.masses))
 
     @property
     def n_traj(self) -> int:

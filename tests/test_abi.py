@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_version_and_strerror():
-    assert nu.nu_version() == 10000
+    assert nu.nu_version() == 10100
     for code in range(0, -10, -1):
         assert nu.strerror(code) != "unknown error"
     assert nu.strerror(-99) == "unknown error"
@@ -123,3 +123,29 @@ def test_create_without_gpu_fails_loudly():
     with pytest.raises(nu.NuError) as e:
         nu.nu_profile_create(cosmo, halo, relic, radii, grid, opts)
     assert e.value.code in (nu.NU_ECUDA, nu.NU_ENOMEM)
+
+
+def test_mass_reuse_plan_and_validation():
+    pb = W.plain_small(precision=W.MIXED)[0]
+    one = nu.plan(pb)
+    assert one["n_masses"] == 1
+    many = nu.plan(pb.replace(masses=(0.01, 0.05, 0.3)))
+    assert many["n_masses"] == 3 and many["n_traj"] == one["n_traj"]
+    assert many["device_bytes"] > one["device_bytes"]
+    for bad in ((0.1, 0.0), (0.1, -1.0), (float("nan"),), tuple([0.1] * (nu.NU_MAX_MASSES + 1))):
+        with pytest.raises(nu.NuError) as e:
+            nu.plan(pb.replace(masses=bad))
+        assert e.value.code == nu.NU_EINVAL
+    cosmo, halo, relic, radii, grid, opts = nu.structs(pb, torch_alloc=False)
+    relic.n_masses = 2                      # a count without a list
+    with pytest.raises(nu.NuError) as e:
+        nu.nu_profile_plan(cosmo, halo, relic, radii, grid, opts)
+    assert e.value.code == nu.NU_EINVAL
+
+
+def test_noalloc_refuses_mass_reuse_before_touching_the_gpu():
+    pb = W.plain_small(precision=W.MIXED)[0].replace(masses=(0.05, 0.1))
+    cosmo, halo, relic, radii, grid, opts = nu.structs(pb, torch_alloc=False)
+    with pytest.raises(nu.NuError) as e:
+        nu.nu_profile_compute_noalloc(cosmo, halo, relic, radii, grid, None)
+    assert e.value.code == nu.NU_ENOTSUP

@@ -386,3 +386,34 @@ def test_initial_speed_scale_matches_textbook_mean_speed():
     # the equations are mass-free: (m, q) and (2m, 2q) start at the same velocity
     assert np.allclose(oracle.initial_state(halo(m_eV=0.2), 5.0, 3.0, 0.1),
                        oracle.initial_state(halo(m_eV=0.4), 5.0, 6.0, 0.1), rtol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Sec. III: one trajectory set read for many relic masses
+# --------------------------------------------------------------------------
+
+def test_mass_reuse_reads_the_fiducial_mass_bit_for_bit():
+    pb = W.plain_small(precision=W.FP64)[0].replace(n_q=16, n_mu=6, n_steps=120)
+    m = oracle.profile_masses(pb, [pb.m_eV, 0.3])
+    assert np.array_equal(m[0], oracle.profile(pb))
+
+
+def test_mass_reuse_equals_direct_runs_with_scaled_grids():
+    # Mass m_a on the fiducial grid scaled by s_a = m_a/m starts every
+    # trajectory at the fiducial velocity; a direct run at m_a on the scaled
+    # q range must agree (exactly up to rounding where the map is well conditioned).
+    pb = W.plain_small(precision=W.FP64)[0].replace(radii=np.array([100.0, 300.0]), n_q=24, n_mu=10)
+    masses = [0.02, 0.05, 0.25, 0.6]
+    m = oracle.profile_masses(pb, masses)
+    for a, ma in enumerate(masses):
+        s = ma / pb.m_eV
+        b = oracle.profile(pb.replace(m_eV=ma, q_min=pb.q_min * s, q_max=pb.q_max * s))
+        assert np.allclose(m[a], b, rtol=1e-6, atol=0), (ma, m[a], b)
+    # heavier relics cluster more (Sec. III, Fig. 1)
+    assert np.all(np.diff(m[:, 0]) > 0)
+
+
+def test_mass_reuse_massless_halo_gives_background_for_every_mass():
+    pb = W.plain_small(precision=W.FP64)[0].replace(M_h=0.0, n_q=20, n_mu=4, n_steps=40)
+    m = oracle.profile_masses(pb, [0.01, 0.1, 0.5])
+    assert np.allclose(m, 1.0, rtol=1e-13, atol=0)
