@@ -106,6 +106,22 @@ __device__ __forceinline__ double nfw_I(double y)
 // Steps between two tests of the early exit (a power of two).
 constexpr int kExitEvery = 4;
 
+// A trajectory is finished when its velocity can no longer change: it lies
+// beyond R, where the gradient is exactly zero (mass compensation, App. A),
+// and the straight line it follows from there along the integration direction
+// (-v: the backward step moves it along -v) never comes back within R.  That
+// holds when it recedes (x . v <= 0), or when the line's closest approach to
+// the centre, b^2 = r^2 - (x . v)^2 / v^2, stays beyond R (App. B's criterion
+// for rays that miss the halo, here exact because nothing acts outside R).
+// The factor kMiss on R^2 keeps the test safe against the rounding of the
+// stepped positions (relative deviations below 1e-4 from the straight line).
+template <typename T>
+__device__ __forceinline__ bool escapes(T r2, T dot, T v2, T R2)
+{
+    const T kMiss = T(1.001);
+    return r2 >= R2 && (dot <= T(0) || (r2 - kMiss * R2) * v2 >= dot * dot);
+}
+
 struct HaloF32 { float invIc, invR3, R2; };
 struct HaloF64 { double invIc, invR3, R2; };
 
@@ -542,11 +558,9 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             }
         }
 
-        // A trajectory beyond R whose position recedes along the integration
-        // direction (x . v <= 0: the backward step moves it along -v) never
-        // re-enters: the gradient is exactly zero there (mass compensation),
-        // so every later step leaves v unchanged and q_i depends on v alone.
-        // A warp stops integrating once all of its lanes are in that state
+        // A finished trajectory (escapes(): beyond R on a line that never
+        // re-enters) keeps its velocity for every later step, and q_i depends
+        // on v alone.  A warp stops integrating once all of its lanes are in that state
         // (padding lanes of a ragged tile start finished); the test runs every
         // kExitEvery steps, and a finished lane that keeps stepping with its
         // warp stays beyond R with its velocity unchanged.  All lanes of the
@@ -560,8 +574,9 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                 if (((n - s_begin) & (kExitEvery - 1)) == 0) {
                     const f2 r2 = fma2(X, X, mul2(Y, Y));
                     const f2 dot = fma2(X, VX, mul2(Y, VY));
-                    const bool fin0 = !act[0] || (f2lo(r2) >= hc.R2 && f2lo(dot) <= 0.0f);
-                    const bool fin1 = !act[1] || (f2hi(r2) >= hc.R2 && f2hi(dot) <= 0.0f);
+                    const f2 v2 = fma2(VX, VX, mul2(VY, VY));
+                    const bool fin0 = !act[0] || escapes(f2lo(r2), f2lo(dot), f2lo(v2), hc.R2);
+                    const bool fin1 = !act[1] || escapes(f2hi(r2), f2hi(dot), f2hi(v2), hc.R2);
                     done |= fin0 && fin1;
                     if (__all_sync(0xffffffffu, done)) break;
                 }
@@ -581,8 +596,9 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                     bool fin = true;
 #pragma unroll
                     for (int i = 0; i < TPT; ++i) {
-                        fin_i[i] = !act[i] || (fma(x[i], x[i], y[i] * y[i]) >= hc.R2 &&
-                                               fma(x[i], vx[i], y[i] * vy[i]) <= T(0));
+                        fin_i[i] = !act[i] || escapes(fma(x[i], x[i], y[i] * y[i]),
+                                                      fma(x[i], vx[i], y[i] * vy[i]),
+                                                      fma(vx[i], vx[i], vy[i] * vy[i]), hc.R2);
                         fin &= fin_i[i];
                     }
                     done |= fin;

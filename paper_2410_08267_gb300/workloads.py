@@ -115,6 +115,23 @@ def precision_sweep(precision: int = MIXED, masses=PRECISION_SWEEP_MASSES,
             for m in masses]
 
 
+def precision_sweep_reuse(precision: int = MIXED, masses=PRECISION_SWEEP_MASSES,
+                          n_radii: int = 64, n_mu: int = 64, n_steps: int = 800) -> Problem:
+    """The precision sweep as ONE mass-reuse request (Sec. III): trajectories
+    for the heaviest mass, read for every mass.  Each mass's own 0.01-10 k_B T0
+    range maps to 0.01 (m_fid/m) .. 10 (m_fid/m) on the fiducial grid, so the
+    grid spans the union, log-spaced at the per-mass density (200 nodes per
+    three decades)."""
+    m_fid = max(masses)
+    q_min, q_max = 0.01, 10.0 * m_fid / min(masses)
+    n_q = int(round(200 * np.log10(q_max / q_min) / 3.0))
+    M = 1e13
+    return Problem(M_h=M, c=c_of_M(M), xi_kind=XI_EXP, xi_p=(0.8, 0.0, 0.0), m_eV=m_fid,
+                   radii=np.geomspace(1.0, 1000.0, n_radii), n_q=n_q, q_min=q_min,
+                   q_max=q_max, n_mu=n_mu, n_steps=n_steps, z_end=4.0, precision=precision,
+                   masses=tuple(masses))
+
+
 def batched_uneven(n_halos: int = 1024, seed: int = 2410, precision: int = MIXED,
                    n_steps: int = 400) -> List[Problem]:
     """1024 halos: log10 M ~ U[11,15], c lognormal (0.15 dex) about the c-M law,

@@ -185,3 +185,31 @@ def test_packed_path_is_bitwise_the_two_trajectory_path(block):
                 nu.nu_profile_destroy(h)
         for a, b in zip(outs[0], outs[1]):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.MIXED])
+def test_rays_that_miss_the_halo_stop_at_once(prec):
+    """Radii beyond R (App. B's regime): a trajectory whose straight path never
+    comes within R keeps its momentum, and the kernel stops it at its first
+    test; the results still equal the oracle's full integration."""
+    pb0 = W.plain_small(precision=prec)[0]
+    R = oracle.derive(pb0)["R"]
+    pb = pb0.replace(radii=np.array([0.5, 1.5, 4.0, 20.0]) * R, n_q=24, n_mu=16, n_steps=200)
+    got = _qi(pb)
+    _, ref = oracle.profile(pb, return_qi=True)
+    e = rel_err(got, ref)
+    assert np.median(e) < (1e-13 if prec == W.FP64 else 1e-6)
+    q0 = oracle.log_grid(pb.n_q, pb.q_min, pb.q_max)[0]
+    # at 20 R no GL direction passes within R: every q_i is its start q
+    assert np.allclose(got[3], q0[:, None], rtol=(1e-14 if prec == W.FP64 else 1e-6))
+    assert_parity(nu.profile(pb)[0], pb, where="beyond R")
+    # the counting run sees far fewer integrated steps than the nominal ones
+    h = nu.create(pb)
+    b = nu.nu_batch_create([h])
+    try:
+        c = nu.nu_batch_branch_counts(b)
+        live_far = c[4]
+    finally:
+        nu.nu_batch_destroy(b)
+        nu.nu_profile_destroy(h)
+    assert live_far < 0.6 * pb.traj_steps, (live_far, pb.traj_steps)
