@@ -61,7 +61,7 @@ SMS, FP32_LANES_PER_SM = 152, 128
 # (dram__bytes_read.sum + dram__bytes_write.sum), recorded in
 # profiles/traj_kernel_precision_sweep_mixed.md.  Must be reset to None
 # whenever the kernel changes, until it is captured again.
-NCU_TRAFFIC_BYTES = {}
+NCU_TRAFFIC_BYTES = {"128x3xg": 697984.0}
 SAMPLE_RADII = (0, 21, 42, 63)
 SAMPLE_MASS_INDEX = 2          # 0.1 eV
 
@@ -357,7 +357,7 @@ def bench_ours(args):
 
     # ---- the same four masses from one trajectory set (Sec. III mass reuse) ----
     reuse = None
-    if args.case == "full":
+    if args.case == "full" and not args.main_only:
         rpb, rms, rout = mass_reuse_once(nu, torch, stream, block, tpt, tflags,
                                          max(3, min(args.steps, 10)), flush)
         kms_main = float(np.mean(kernel_ms))
@@ -373,7 +373,7 @@ def bench_ours(args):
 
     # ---- serving: the request stream, continuous batching vs one launch per request ----
     serving = None
-    if args.serve_rate > 0 and args.case == "full":
+    if args.serve_rate > 0 and args.case == "full" and not args.main_only:
         n_req = args.serve_requests
         serving = {"continuous": serve_once(nu, args.serve_rate, n_req, batched=True),
                    "one_per_launch": serve_once(nu, args.serve_rate, n_req, batched=False)}
@@ -472,6 +472,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=300.0,
                     help="request rate of the serving leg (0: skip it)")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--main-only", action="store_true",
+                    help="skip the serving and mass-reuse legs (profiler runs)")
     ap.add_argument("--serve-sweep", action="store_true",
                     help="only the serving workload at rates 10..5000 /s, one JSON line per rate and mode")
     args = ap.parse_args()
