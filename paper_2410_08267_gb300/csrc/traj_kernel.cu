@@ -5,11 +5,12 @@
 // (Eq. eoms), the force being the closed-form gradient of the compensated,
 // growing NFW halo (App. A).  The state (x, y, vx, vy) stays in registers for
 // the whole integration; the per-step coefficients (background, growth,
-// coupling at the three RK stage times, built in FP64 on the host) are staged
-// once per request into shared memory and read as broadcast vector loads.
-// At the end the Liouville map f0 = f_init(P_i) (Sec. II.C) and the weight of
-// the trajectory in Eq. localdensity are applied, and the tile's sum is formed
-// by a warp-shuffle + shared-memory tree.  Tile sums land in a per-request
+// coupling at the three RK stage times, built in FP64 on the host) are read as
+// warp-uniform vector loads, either staged once per request into shared memory
+// or (GTAB) in place through the L1 cache.  At the end the Liouville map
+// f0 = f_init(P_i) (Sec. II.C) and the weight of the trajectory in
+// Eq. localdensity are applied, once per relic mass read from the trajectory
+// (Sec. III), and each tile's sum is formed by a warp-shuffle + shared-memory tree.  Tile sums land in a per-request
 // array; the CTA that completes the last tile of a radius adds them in tile
 // order (so every result is bitwise independent of scheduling and of what
 // else shares the launch) and writes n/nbar.
