@@ -376,8 +376,11 @@ void nu_server::run()
         if (rc != NU_OK) {
             cudaGetLastError();
             {
+                // the server stops admitting: queued requests fail with the same status
                 std::lock_guard<std::mutex> g(mu);
                 fatal = rc;
+                for (auto& p : pending) done[p.ticket] = Done{rc, {}, {}, ms_since(p.t_submit)};
+                pending.clear();
             }
             if (rc == NU_ETIMEDOUT) {
                 // the GPU may still be running the launch: fail the requests but

@@ -165,3 +165,28 @@ def test_fp64_server():
             assert rc == nu.NU_OK and np.array_equal(out, _alone(pb, block=256, tpt=1)[0])
     finally:
         nu.nu_server_destroy(srv)
+
+
+def test_launch_over_its_time_limit_fails_requests_and_stops_the_server():
+    """Failure detection without a GPU fault: a time limit far below one
+    launch's duration makes the bounded wait run out.  The kernel itself
+    finishes normally; the server reports NU_ETIMEDOUT for the requests it
+    carried and for the queued ones, refuses new work, and the context stays
+    usable."""
+    probs = _stream(6, seed=31, max_radii=64, n_steps=400)
+    srv = nu.nu_server_create(64 << 20, precision=W.MIXED, chunk_steps=0, max_active=2,
+                              gpu_timeout_ms=1e-3)
+    try:
+        tickets = [nu.nu_server_submit(srv, pb) for pb in probs]
+        codes = [_wait(srv, t, pb.n_radii)[0] for t, pb in zip(tickets, probs)]
+        assert codes == [nu.NU_ETIMEDOUT] * len(probs)
+        with pytest.raises(nu.NuError) as e:
+            nu.nu_server_submit(srv, probs[0])
+        assert e.value.code == nu.NU_ETIMEDOUT
+        assert nu.nu_server_stats(srv)["status"] == nu.NU_ETIMEDOUT
+    finally:
+        nu.nu_server_destroy(srv)
+    import torch
+    torch.cuda.synchronize()
+    out, _ = nu.profile(probs[0].replace(n_steps=50))
+    assert np.all(np.isfinite(out))
