@@ -87,6 +87,12 @@ extern "C" {
 /* ---- initial relic distribution f(q), q = P / (k_B T0) (Sec. II.C, IV.B) -- */
 #define NU_F_FD        0   /* Fermi-Dirac 1/(1+exp(q - eta)); f_p[0] = eta     */
 #define NU_F_FREEZEIN  1   /* non-thermal q^(-1/2) exp(-q)                     */
+#define NU_F_TABLE     2   /* tabulated f (the spectral distortions and other
+                              relics of Sec. IV.B): f_table[k] = f(q_k) at
+                              q_k = f_p[0] (f_p[1]/f_p[0])^(k/(n_table-1)),
+                              k = 0 .. n_table-1; f is linear in ln q between
+                              nodes, f_table[0] below f_p[0] and 0 above f_p[1] */
+#define NU_MAX_FTABLE  4096
 
 /* ---- precision modes ------------------------------------------------------ */
 #define NU_FP64   0        /* state, force, f and sums in FP64                 */
@@ -141,8 +147,11 @@ typedef struct nu_relic {
     double m_eV;     /* relic mass, eV (> 0); the fiducial mass if n_masses > 0 */
     int f_kind;      /* NU_F_*                                                 */
     int n_masses;    /* 0: one mass m_eV; 1 .. NU_MAX_MASSES: masses_eV        */
-    double f_p[2];
+    double f_p[2];   /* FD: {eta, -}; table: {q_first, q_last} in k_B T0     */
     const double* masses_eV;   /* [n_masses] relic masses, eV (> 0)            */
+    int n_table;     /* NU_F_TABLE: nodes (2 .. NU_MAX_FTABLE)                 */
+    int reserved;
+    const double* f_table;     /* NU_F_TABLE: [n_table] values >= 0, borrowed  */
 } nu_relic;
 
 typedef struct nu_pgrid {
@@ -381,7 +390,7 @@ NU_API int nu_server_submit(nu_server* s, const nu_cosmo* cosmo, const nu_halo* 
  * returns the request's status (NU_OK, NU_ECANCELED, NU_ENOMEM, NU_ETIMEDOUT ...)
  * once; NU_EINVAL for an unknown or already delivered ticket or a wrong n_radii
  * (for a mass-reuse request, n_masses times its number of radii; the server
- * keeps its own copy of the mass list). */
+ * keeps its own copies of the mass list and of a tabulated f). */
 NU_API int nu_server_poll(nu_server* s, long long ticket, double* n_over_nbar, double* err_est,
                           int n_radii, double* latency_ms);
 /* Cancel a queued or running request (it completes with NU_ECANCELED before
@@ -417,8 +426,9 @@ NU_API void nu_server_destroy(nu_server* s);
  *   never overlap; any other work that touched the array while a call ran
  *   would race with it.  The array keeps the last call's contents; each call
  *   clears the counters that must start at zero.
- *   Errors: NU_EINVAL, NU_ENOTSUP (the packed shape tpt = 3, or a mass-reuse
- *   relic: this entry point computes one mass), NU_ETOOBIG (the request needs
+ *   Errors: NU_EINVAL, NU_ENOTSUP (the packed shape tpt = 3, a mass-reuse
+ *   relic or a tabulated f: this entry point computes one closed-form
+ *   distribution for one mass), NU_ETOOBIG (the request needs
  *   more than NU_NOALLOC_MAX_BYTES, e.g. too many radii x tiles or steps),
  *   NU_EDEVICE, NU_ECUDA. */
 NU_API int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* halo,

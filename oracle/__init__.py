@@ -35,8 +35,8 @@ class OrParams(C.Structure):
                 ("M_h", C.c_double), ("c", C.c_double), ("z0", C.c_double),
                 ("xi_kind", C.c_int), ("kappa_kind", C.c_int),
                 ("xi_p", C.c_double * 3), ("kappa_p", C.c_double * 3),
-                ("m_eV", C.c_double), ("f_kind", C.c_int), ("pad_", C.c_int),
-                ("f_p", C.c_double * 2)]
+                ("m_eV", C.c_double), ("f_kind", C.c_int), ("n_table", C.c_int),
+                ("f_p", C.c_double * 2), ("f_table", C.POINTER(C.c_double))]
 
 
 class OrDerived(C.Structure):
@@ -110,6 +110,10 @@ def params(pb) -> OrParams:
         p.kappa_p[i] = float(pb.kappa_p[i])
     p.m_eV = pb.m_eV
     p.f_kind = int(pb.f_kind)
+    if len(getattr(pb, "f_table", ())):
+        p._tab = np.ascontiguousarray(np.asarray(pb.f_table, dtype=np.float64))
+        p.n_table = len(p._tab)
+        p.f_table = p._tab.ctypes.data_as(C.POINTER(C.c_double))
     p.f_p[0], p.f_p[1] = float(pb.f_p[0]), float(pb.f_p[1])
     return p
 

@@ -58,7 +58,7 @@
 /* Halo-growth and coupling kinds (same meaning as the library's enums). */
 enum { OR_XI_STATIC = 0, OR_XI_LINEAR = 1, OR_XI_EXP = 2 };
 enum { OR_KAPPA_ONE = 0, OR_KAPPA_POW1PZ = 1, OR_KAPPA_PAPER = 2, OR_KAPPA_CONST = 3 };
-enum { OR_F_FD = 0, OR_F_FREEZEIN = 1 };
+enum { OR_F_FD = 0, OR_F_FREEZEIN = 1, OR_F_TABLE = 2 };
 
 typedef struct {
     double Om, h, T0_K;                 /* cosmology (Sec. II.A)               */
@@ -66,8 +66,9 @@ typedef struct {
     int xi_kind, kappa_kind;
     double xi_p[3], kappa_p[3];
     double m_eV;                        /* relic mass                          */
-    int f_kind, pad_;
+    int f_kind, n_table;                /* n_table: nodes of a tabulated f     */
     double f_p[2];
+    const double* f_table;              /* tabulated f values (kind 2)         */
 } or_params;
 
 typedef struct {
@@ -284,6 +285,18 @@ double or_f(const or_params* p, double q)
     switch (p->f_kind) {
     case OR_F_FD:          /* Fermi-Dirac (reading R3) */
         return 1.0 / (1.0 + exp(q - p->f_p[0]));
+    case OR_F_TABLE: {     /* tabulated f (Sec. IV.B distributions): nodes q_k log-spaced
+                              from f_p[0] to f_p[1]; linear in ln q between nodes,
+                              the first value below the range and 0 above it */
+        int n = p->n_table;
+        if (q <= p->f_p[0]) return p->f_table[0];
+        if (q > p->f_p[1]) return 0.0;
+        double pos = (double)(n - 1) * (log(q) - log(p->f_p[0])) / (log(p->f_p[1]) - log(p->f_p[0]));
+        int k = (int)floor(pos);
+        if (k >= n - 1) return p->f_table[n - 1];
+        double frac = pos - (double)k;
+        return (1.0 - frac) * p->f_table[k] + frac * p->f_table[k + 1];
+    }
     case OR_F_FREEZEIN:    /* non-thermal q^(-1/2) e^(-q) */
         if (q < 1e-300) q = 1e-300;
         return exp(-q) / sqrt(q);

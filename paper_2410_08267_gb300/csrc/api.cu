@@ -167,7 +167,9 @@ int plan_common(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* reli
     const int tps_alloc = (int)((seg + kMinTile - 1) / kMinTile);
     info.device_bytes = device_bytes(o.precision, o.n_steps, n_radii, grid->n_q, grid->n_mu,
                                      tps_alloc, (o.flags & NU_FLAG_KEEP_QI) != 0,
-                                     relic_n_mass(*relic), &info.h2d_bytes);
+                                     relic_n_mass(*relic),
+                                     relic->f_kind == NU_F_TABLE ? relic->n_table : 0,
+                                     &info.h2d_bytes);
     const long long nt = (long long)tiles_per_seg * n_radii;
     if (nt > (1LL << 30)) return NU_EINVAL;
     info.n_tiles = (int)nt;
@@ -273,6 +275,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     h->halo = *halo;
     h->relic = *relic;
     h->relic.masses_eV = nullptr;                         // borrowed: not kept
+    h->relic.f_table = nullptr;
     h->grid = *p_grid;
     h->opts = o;
     h->d = d;
@@ -328,6 +331,8 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     const size_t o_wqc = carve((size_t)nq * sizeof(double));
     const size_t o_wmu = carve((size_t)nmu * sizeof(double));
     const size_t o_mass = carve((size_t)nm * 3 * sizeof(double));   // scales, then norms
+    const int nft = relic->f_kind == NU_F_TABLE ? relic->n_table : 0;
+    const size_t o_ftab = carve((size_t)(nft > 0 ? nft : 1) * sz);   // tabulated f
     const size_t upload_end = off;                         // everything above is uploaded
     // tile sums sized for the smallest tile shape, so that any batch shape fits
     const size_t tps_alloc = (size_t)(((long long)nq * nmu + kMinTile - 1) / kMinTile);
@@ -368,6 +373,13 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     P.R2 = d.R * d.R;
     P.f_p0 = relic->f_p[0];
     P.f_kind = relic->f_kind;
+    if (nft > 0) {
+        P.n_ftab = nft;
+        P.ftab = base + o_ftab;
+        P.ftab_q0 = relic->f_p[0];
+        P.ftab_q1 = relic->f_p[1];
+        P.ftab_scale = (nft - 1) / std::log(relic->f_p[1] / relic->f_p[0]);
+    }
     P.n_radii = n_radii;
     P.n_q = nq;
     P.n_mu = nmu;
@@ -401,6 +413,10 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     put<double>(stage, o_wmu, wmu.data(), nmu);
     put<double>(stage, o_mass, mass_s.data(), nm);
     put<double>(stage, o_mass + nm * sizeof(double), norms.data(), 2 * (size_t)nm);
+    if (nft > 0) {
+        if (fp64) put<double>(stage, o_ftab, relic->f_table, nft);
+        else put<float>(stage, o_ftab, relic->f_table, nft);
+    }
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
     if (cudaMemcpyAsync(base, stage.data(), upload_end, cudaMemcpyHostToDevice, s) != cudaSuccess ||

@@ -36,7 +36,14 @@ int validate(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
         if (zs > 0.0 && ze > 0.0 && !(zs > ze)) return NU_EINVAL;
     }
     if (!(relic->m_eV > 0.0) || !std::isfinite(relic->m_eV)) return NU_EINVAL;
-    if (relic->f_kind < NU_F_FD || relic->f_kind > NU_F_FREEZEIN) return NU_EINVAL;
+    if (relic->f_kind < NU_F_FD || relic->f_kind > NU_F_TABLE) return NU_EINVAL;
+    if (relic->f_kind == NU_F_TABLE) {                // tabulated f (Sec. IV.B)
+        if (!relic->f_table || relic->n_table < 2 || relic->n_table > NU_MAX_FTABLE) return NU_EINVAL;
+        if (!(relic->f_p[0] > 0.0) || !(relic->f_p[1] > relic->f_p[0]) || !std::isfinite(relic->f_p[1]))
+            return NU_EINVAL;
+        for (int k = 0; k < relic->n_table; ++k)
+            if (!(relic->f_table[k] >= 0.0) || !std::isfinite(relic->f_table[k])) return NU_EINVAL;
+    }
     if (relic->n_masses < 0 || relic->n_masses > NU_MAX_MASSES) return NU_EINVAL;
     if (relic->n_masses > 0) {                        // mass reuse (Sec. III)
         if (!relic->masses_eV) return NU_EINVAL;
@@ -123,6 +130,17 @@ double coupling_kappa(const nu_halo& halo, double z)
 // (Sec. II.C) or the non-thermal q^(-1/2) e^(-q) shape.
 double relic_f(const nu_relic& relic, double q)
 {
+    if (relic.f_kind == NU_F_TABLE) {
+        // linear in ln q between log-spaced nodes; f_table[0] below, 0 above
+        const int n = relic.n_table;
+        if (!(q > relic.f_p[0])) return relic.f_table[0];
+        if (q > relic.f_p[1]) return 0.0;
+        const double u = std::log(q / relic.f_p[0]) * (n - 1) / std::log(relic.f_p[1] / relic.f_p[0]);
+        if (u >= n - 1) return relic.f_table[n - 1];
+        const int k = (int)u;
+        const double w = u - k;
+        return relic.f_table[k] + w * (relic.f_table[k + 1] - relic.f_table[k]);
+    }
     if (relic.f_kind == NU_F_FREEZEIN) {
         const double qq = q > 1e-300 ? q : 1e-300;
         return std::exp(-qq) / std::sqrt(qq);
@@ -284,7 +302,7 @@ static void gauss_legendre_compute(int n, std::vector<double>& x, std::vector<do
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_mu,
-                       int tiles_per_seg, bool keep_qi, int n_mass, long long* h2d_bytes)
+                       int tiles_per_seg, bool keep_qi, int n_mass, int n_ftab, long long* h2d_bytes)
 {
     const size_t sz = precision == NU_FP64 ? sizeof(double) : sizeof(float);
     size_t b = 0;
@@ -299,6 +317,7 @@ long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_m
     b += 2 * align256((size_t)n_q * sizeof(double));             // wq, wqc
     b += align256((size_t)n_mu * sizeof(double));                // wmu
     b += align256((size_t)n_mass * 3 * sizeof(double));          // mass scales, normalisations
+    b += align256((size_t)(n_ftab > 0 ? n_ftab : 1) * sz);       // tabulated f
     if (h2d_bytes) *h2d_bytes = (long long)b;                    // everything above is uploaded
     b += align256((size_t)n_radii * tiles_per_seg * 2 * n_mass * sizeof(double));
     b += align256((size_t)n_radii * sizeof(unsigned));

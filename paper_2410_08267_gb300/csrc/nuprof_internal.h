@@ -70,7 +70,7 @@ void log_nodes(int n, double q_min, double q_max, std::vector<double>& q,
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 void resolve_opts(const nu_opts* in, nu_opts& out);
 long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_mu,
-                       int tiles_per_seg, bool keep_qi, int n_mass, long long* h2d_bytes);
+                       int tiles_per_seg, bool keep_qi, int n_mass, int n_ftab, long long* h2d_bytes);
 // Number of masses read from one trajectory set (Sec. III mass reuse).
 inline int relic_n_mass(const nu_relic& r) { return r.n_masses > 0 ? r.n_masses : 1; }
 
@@ -97,6 +97,11 @@ struct DevProblem {
     double invIc, invR3, R2;
     double f_p0;
     int f_kind;
+    int n_ftab;             // NU_F_TABLE: nodes of ftab
+    const void* ftab;       // NU_F_TABLE: [n_ftab] f values in the state precision
+    double ftab_q0;         // first node (k_B T0)
+    double ftab_q1;         // last node
+    double ftab_scale;      // (n_ftab - 1) / ln(q_last / q_first)
     int n_radii, n_q, n_mu, n_steps;
     int tiles_per_seg, tile;
     int precision;

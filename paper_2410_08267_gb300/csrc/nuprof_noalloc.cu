@@ -195,6 +195,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     if (o.flags != 0) return NU_EINVAL;
     if (o.tpt == kTptPacked) return NU_ENOTSUP;   // the packed table is not staged here
     if (relic && relic->n_masses > 0) return NU_ENOTSUP;   // one mass per call
+    if (relic && relic->f_kind == NU_F_TABLE) return NU_ENOTSUP;   // closed-form f only
     int rc = validate(cosmo, halo, relic, radii, n_radii, p_grid, &o);
     if (rc != NU_OK) return rc;
     Derived d;

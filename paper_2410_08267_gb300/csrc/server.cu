@@ -120,8 +120,13 @@ struct Pending {
     nu_opts opts;
     std::vector<double> radii;
     std::vector<double> masses;   // relic masses of a mass-reuse request (owned copy)
+    std::vector<double> ftable;   // tabulated f (owned copy)
     Clock::time_point t_submit;
-    void fix() { relic.masses_eV = masses.empty() ? nullptr : masses.data(); }
+    void fix()
+    {
+        relic.masses_eV = masses.empty() ? nullptr : masses.data();
+        relic.f_table = ftable.empty() ? nullptr : ftable.data();
+    }
 };
 
 struct Active {
@@ -516,6 +521,8 @@ int nu_server_submit(nu_server* s, const nu_cosmo* cosmo, const nu_halo* halo, c
     p.radii.assign(radii, radii + n_radii);
     if (relic->n_masses > 0 && relic->masses_eV)
         p.masses.assign(relic->masses_eV, relic->masses_eV + std::min(relic->n_masses, NU_MAX_MASSES));
+    if (relic->f_kind == NU_F_TABLE && relic->f_table && relic->n_table > 0)
+        p.ftable.assign(relic->f_table, relic->f_table + std::min(relic->n_table, NU_MAX_FTABLE));
     p.fix();
     nu_plan_info info;
     const int rc = nu_profile_plan(&p.cosmo, &p.halo, &p.relic, radii, n_radii, &p.grid, &p.opts, &info);

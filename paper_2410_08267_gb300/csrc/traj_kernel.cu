@@ -231,21 +231,42 @@ template <> struct PrecTraits<double> {
 };
 
 // Initial distribution f(q) (Sec. II.C, Sec. IV.B) in the state precision.
-__device__ __forceinline__ float relic_f_dev(int kind, float eta, float q)
+// The tabulated kind is linear in ln q between log-spaced nodes, the first
+// value below the first node and 0 above the last.
+__device__ __forceinline__ float log_T(float v) { return logf(v); }
+__device__ __forceinline__ double log_T(double v) { return log(v); }
+
+template <typename T>
+__device__ __forceinline__ T relic_f_table(const DevProblem& P, T q)
 {
-    if (kind == NU_F_FREEZEIN) {
+    const T* t = reinterpret_cast<const T*>(P.ftab);
+    const int n = P.n_ftab;
+    if (!(q > (T)P.ftab_q0)) return t[0];
+    if (q > (T)P.ftab_q1) return T(0);
+    const T u = log_T(q / (T)P.ftab_q0) * (T)P.ftab_scale;
+    if (u >= T(n - 1)) return t[n - 1];
+    const int k = (int)u;
+    const T w = u - (T)k;
+    return t[k] + w * (t[k + 1] - t[k]);
+}
+
+__device__ __forceinline__ float relic_f_dev(const DevProblem& P, float q)
+{
+    if (P.f_kind == NU_F_TABLE) return relic_f_table<float>(P, q);
+    if (P.f_kind == NU_F_FREEZEIN) {
         const float qq = fmaxf(q, 1e-30f);
         return expf(-qq) * rsqrtf(qq);
     }
-    return 1.0f / (1.0f + expf(q - eta));
+    return 1.0f / (1.0f + expf(q - (float)P.f_p0));
 }
-__device__ __forceinline__ double relic_f_dev(int kind, double eta, double q)
+__device__ __forceinline__ double relic_f_dev(const DevProblem& P, double q)
 {
-    if (kind == NU_F_FREEZEIN) {
+    if (P.f_kind == NU_F_TABLE) return relic_f_table<double>(P, q);
+    if (P.f_kind == NU_F_FREEZEIN) {
         const double qq = fmax(q, 1e-300);
         return exp(-qq) / sqrt(qq);
     }
-    return 1.0 / (1.0 + exp(q - eta));
+    return 1.0 / (1.0 + exp(q - P.f_p0));
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -654,7 +675,7 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
 #pragma unroll
             for (int i = 0; i < TPT; ++i) {
                 if (!act[i]) continue;
-                const double f = (double)relic_f_dev(P.f_kind, (T)P.f_p0, qf[i] * sa);
+                const double f = (double)relic_f_dev(P, qf[i] * sa);
                 const double wm = P.wmu[tk[i]];
                 acc += P.wq[tj[i]] * wm * f;
                 accc += P.wqc[tj[i]] * wm * f;

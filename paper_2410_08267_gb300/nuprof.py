@@ -48,7 +48,8 @@ class nu_halo(C.Structure):
 
 class nu_relic(C.Structure):
     _fields_ = [("m_eV", C.c_double), ("f_kind", C.c_int), ("n_masses", C.c_int),
-                ("f_p", C.c_double * 2), ("masses_eV", C.POINTER(C.c_double))]
+                ("f_p", C.c_double * 2), ("masses_eV", C.POINTER(C.c_double)),
+                ("n_table", C.c_int), ("reserved", C.c_int), ("f_table", C.POINTER(C.c_double))]
 
 
 class nu_pgrid(C.Structure):
@@ -224,6 +225,10 @@ def structs(pb: "W.Problem", block: int = 0, tpt: int = 0, flags: int = 0, strea
     relic = nu_relic()
     relic.m_eV, relic.f_kind = pb.m_eV, int(pb.f_kind)
     relic.f_p[0], relic.f_p[1] = float(pb.f_p[0]), float(pb.f_p[1])
+    if len(pb.f_table):                     # tabulated f: f_p holds the node range
+        relic._tab = np.ascontiguousarray(np.asarray(pb.f_table, dtype=np.float64))
+        relic.n_table = len(relic._tab)
+        relic.f_table = relic._tab.ctypes.data_as(C.POINTER(C.c_double))
     if len(pb.masses):                      # mass reuse: m_eV is the fiducial mass
         relic._masses = np.ascontiguousarray(np.asarray(pb.masses, dtype=np.float64))
         relic.n_masses = len(relic._masses)

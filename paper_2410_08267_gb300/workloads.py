@@ -25,7 +25,7 @@ XI_STATIC, XI_LINEAR, XI_EXP = 0, 1, 2
 # Coupling kinds (G -> kappa(z) G, Sec. IV.B)
 KAPPA_ONE, KAPPA_POW1PZ, KAPPA_PAPER, KAPPA_CONST = 0, 1, 2, 3
 # Relic distribution kinds (Sec. II.C, Sec. IV.B)
-F_FD, F_FREEZEIN = 0, 1
+F_FD, F_FREEZEIN, F_TABLE = 0, 1, 2
 # Radius units
 RADII_KPC, RADII_R200 = 0, 1
 # Precision modes
@@ -47,7 +47,8 @@ class Problem:
     kappa_p: tuple = (0.0, 0.0, 0.0)
     m_eV: float = 0.1
     f_kind: int = F_FD
-    f_p: tuple = (0.0, 0.0)                # FD chemical potential eta
+    f_p: tuple = (0.0, 0.0)                # FD chemical potential eta; table: q range
+    f_table: tuple = ()                    # F_TABLE: f at log-spaced q from f_p[0] to f_p[1]
     radii: np.ndarray = field(default_factory=lambda: np.geomspace(1.0, 300.0, 10))
     radii_unit: int = RADII_KPC
     n_q: int = 50
@@ -182,6 +183,19 @@ def new_physics(n_halos: int = 256, seed: int = 2411, precision: int = MIXED,
                            n_q=n_q, q_min=0.01, q_max=10.0, n_mu=n_mu, n_steps=n_steps,
                            z_end=4.0, precision=precision))
     return out
+
+
+def spectral_distortions(n_table: int = 512, q_first: float = 1e-3, q_last: float = 40.0):
+    """Tabulated relic distributions of the kinds Sec. IV.B explores (the
+    paper prints no formulas or parameters; these shapes are stand-ins):
+    a thermal spectrum at 0.8 T0 with a Gaussian bump at q = 5, and a cold
+    Fermi gas falling off faster than Fermi-Dirac above q = 3.  Returns
+    {name: (f_p, f_table)} for the F_TABLE kind."""
+    q = np.geomspace(q_first, q_last, n_table)
+    bump = 1.0 / (1.0 + np.exp(q / 0.8)) + 0.05 * np.exp(-0.5 * (q - 5.0) ** 2)
+    cold = 1.0 / (1.0 + np.exp((q - 3.0) / 0.3))
+    return {"thermal_bump": ((q_first, q_last), tuple(float(v) for v in bump)),
+            "cold_fermi_gas": ((q_first, q_last), tuple(float(v) for v in cold))}
 
 
 SERVING_GRIDS = ((64, 16), (128, 32), (256, 64))

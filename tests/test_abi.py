@@ -149,3 +149,20 @@ def test_noalloc_refuses_mass_reuse_before_touching_the_gpu():
     with pytest.raises(nu.NuError) as e:
         nu.nu_profile_compute_noalloc(cosmo, halo, relic, radii, grid, None)
     assert e.value.code == nu.NU_ENOTSUP
+
+
+def test_tabulated_distribution_validation():
+    pb = W.plain_small(precision=W.MIXED)[0]
+    (fp, tab) = W.spectral_distortions()["thermal_bump"]
+    ok = pb.replace(f_kind=W.F_TABLE, f_p=fp, f_table=tab)
+    assert nu.plan(ok)["device_bytes"] > nu.plan(pb)["device_bytes"]
+    for bad in (ok.replace(f_table=tab[:1]), ok.replace(f_p=(0.0, 40.0)),
+                ok.replace(f_p=(5.0, 1.0)), ok.replace(f_table=(-1.0,) + tab[1:]),
+                ok.replace(f_table=(float("inf"),) + tab[1:])):
+        with pytest.raises(nu.NuError) as e:
+            nu.plan(bad)
+        assert e.value.code == nu.NU_EINVAL
+    cosmo, halo, relic, radii, grid, opts = nu.structs(ok, torch_alloc=False)
+    with pytest.raises(nu.NuError) as e:
+        nu.nu_profile_compute_noalloc(cosmo, halo, relic, radii, grid, None)
+    assert e.value.code == nu.NU_ENOTSUP

@@ -417,3 +417,33 @@ def test_mass_reuse_massless_halo_gives_background_for_every_mass():
     pb = W.plain_small(precision=W.FP64)[0].replace(M_h=0.0, n_q=20, n_mu=4, n_steps=40)
     m = oracle.profile_masses(pb, [0.01, 0.1, 0.5])
     assert np.allclose(m, 1.0, rtol=1e-13, atol=0)
+
+
+# --------------------------------------------------------------------------
+# Sec. IV.B: tabulated distributions
+# --------------------------------------------------------------------------
+
+def _table(fun, n=400, q0=1e-3, q1=40.0):
+    q = np.geomspace(q0, q1, n)
+    return q, tuple(float(v) for v in fun(q))
+
+
+def test_table_interpolates_linearly_in_ln_q():
+    q, tab = _table(lambda x: 2.0 + 0.5 * np.log(x), n=7, q0=0.01, q1=10.0)
+    pb = halo(f_kind=W.F_TABLE, f_p=(0.01, 10.0), f_table=tab)
+    for x in (0.0123, 0.5, 3.7, 9.99):
+        assert oracle.f(pb, x) == pytest.approx(2.0 + 0.5 * math.log(x), rel=1e-13)
+    assert oracle.f(pb, 1e-4) == tab[0]
+    assert oracle.f(pb, 10.0) == pytest.approx(tab[-1], rel=1e-15)
+    assert oracle.f(pb, 10.5) == 0.0
+
+
+def test_dense_table_of_fermi_dirac_reproduces_the_closed_form():
+    q, tab = _table(lambda x: 1.0 / (1.0 + np.exp(x)), n=3000, q0=1e-4, q1=60.0)
+    base = W.plain_small(precision=W.FP64)[0].replace(n_q=24, n_mu=8, n_steps=200,
+                                                       radii=np.array([10.0, 100.0]))
+    a = oracle.profile(base)
+    b = oracle.profile(base.replace(f_kind=W.F_TABLE, f_p=(1e-4, 60.0), f_table=tab))
+    assert np.allclose(a, b, rtol=2e-5, atol=0)
+    m0 = base.replace(M_h=0.0, f_kind=W.F_TABLE, f_p=(1e-4, 60.0), f_table=tab)
+    assert np.allclose(oracle.profile(m0), 1.0, rtol=1e-13)
