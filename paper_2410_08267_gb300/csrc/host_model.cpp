@@ -171,9 +171,12 @@ void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, in
         const double rin = std::min(d.r200 * zp1, d.R);
         Q = rin * rin;
     };
+    // the end stage of step n is the start stage of step n + 1: each of the
+    // 2N + 1 half-step stages is evaluated once
+    double Aa, BFa, Sa, Qa;
+    stage(0L, Aa, BFa, Sa, Qa);
     for (int n = 0; n < n_steps; ++n) {
-        double Aa, BFa, Sa, Qa, Am, BFm, Sm, Qm, Ab, BFb, Sb, Qb;
-        stage(2L * n, Aa, BFa, Sa, Qa);
+        double Am, BFm, Sm, Qm, Ab, BFb, Sb, Qb;
         stage(2L * n + 1, Am, BFm, Sm, Qm);
         stage(2L * n + 2, Ab, BFb, Sb, Qb);
         double* t = &tab[(size_t)n * C_COUNT];
@@ -197,6 +200,10 @@ void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, in
         t[C_T1] = Sm / d.Ic;
         t[C_T2] = Sb / d.Ic;
         t[C_PAD] = 0.0;
+        Aa = Ab;
+        BFa = BFb;
+        Sa = Sb;
+        Qa = Qb;
     }
 }
 
