@@ -62,7 +62,7 @@ SMS, FP32_LANES_PER_SM = 152, 128
 # profiles/traj_kernel_precision_sweep_mixed.md.  Must be reset to None
 # whenever the kernel changes, until it is captured again.
 NCU_TRAFFIC_BYTES = {"128x3xg": 697984.0}
-SAMPLE_RADII = (0, 21, 42, 63)
+SAMPLE_RADII = (0, 9, 18, 27, 36, 45, 54, 63)   # oracle sample: ~1 s on 16 cores
 SAMPLE_MASS_INDEX = 2          # 0.1 eV
 
 
@@ -146,7 +146,8 @@ def bench_reference(args):
     if rank != 0:
         return 0
     problems = W.precision_sweep(precision=W.MIXED)
-    sample = (f"m_nu=0.1 eV, radii {list(SAMPLE_RADII)} of 64 (4 x 12800 trajectories x 800 steps)")
+    sample = (f"m_nu=0.1 eV, radii {list(SAMPLE_RADII)} of 64 "
+              f"({len(SAMPLE_RADII)} x 12800 trajectories x 800 steps)")
     for _ in range(args.warmup):
         run_oracle_sample(problems)
     times, ts, cores = [], 0, 1
@@ -262,6 +263,10 @@ def bench_ours(args):
     one = W.precision_sweep(precision=W.MIXED)
     if args.case == "small":            # profiling case: one mass, 24 radii (fills every SM)
         one = [one[SAMPLE_MASS_INDEX].replace(radii=np.geomspace(1.0, 1000.0, 24))]
+    elif args.case == "uneven":         # 1024 halos of uneven sizes in one launch
+        one = W.batched_uneven(precision=W.MIXED)
+    elif args.case == "new_physics":    # 256 halos, relic kinds and couplings
+        one = W.new_physics(precision=W.MIXED)
     # The job at N GPUs is N copies of the workload (weak scaling); its
     # requests are partitioned over the ranks by trajectory-steps, with no
     # collective on the data path.
@@ -412,11 +417,24 @@ def bench_ours(args):
         rel = np.abs(got - ref[list(SAMPLE_RADII)]) / np.abs(ref[list(SAMPLE_RADII)])
     else:
         rel = np.array([np.nan])
+    # per-core rate: one thread on the outermost sampled radius
+    import oracle
+    pb1 = full[SAMPLE_MASS_INDEX].replace(precision=W.FP64)
+    t1 = time.perf_counter()
+    oracle.profile(pb1, radius_sel=[SAMPLE_RADII[-1]], n_threads=1)
+    dt1 = time.perf_counter() - t1
     cpu = {"value": ts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"m_nu=0.1 eV, radii {list(SAMPLE_RADII)} of 64, FP64, {dt:.1f} s wall"}
+           "sample": f"m_nu=0.1 eV, radii {list(SAMPLE_RADII)} of 64, FP64, {dt:.1f} s wall",
+           "per_core_value": pb1.n_q * pb1.n_mu * pb1.n_steps / dt1}
 
     if args.case == "small":
         WORKLOAD_USED = "small profiling case of " + WORKLOAD + " (m_nu=0.1 eV, 24 radii)"
+    elif args.case == "uneven":
+        WORKLOAD_USED = ("batched_uneven: 1024 halos (seed 2410), log10 M ~ U[11,15], n_r ~ U{8..128} "
+                         "x n_q ~ U{32..256} x n_mu ~ U{16..64}, linear growth, 400 RK4 steps z 0->4")
+    elif args.case == "new_physics":
+        WORKLOAD_USED = ("new_physics: 256 halos (seed 2411), 128 radii x 256 log q x 64 GL mu each, "
+                         "FD eta in {-1,0,1} or freeze-in at 1-10 keV, kappa = (1+z)^gamma, 400 steps")
     else:
         WORKLOAD_USED = WORKLOAD
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -440,7 +458,7 @@ def bench_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clock,
             "accuracy": {"max_rel_err_vs_oracle": float(rel.max()),
                          "per_radius": [float(x) for x in rel],
-                         "sample": "m_nu=0.1 eV, radii 0,21,42,63"}}
+                         "sample": f"m_nu=0.1 eV, radii {list(SAMPLE_RADII)} of 64"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -467,8 +485,9 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--shape", default="auto",
                     help="launch shape BLOCKxTPT[xg] (e.g. 256x1, 256x3xg), or auto (autotuner)")
-    ap.add_argument("--case", choices=("full", "small"), default="full",
-                    help="small: one mass x 24 radii of the same workload, for profiler captures")
+    ap.add_argument("--case", choices=("full", "small", "uneven", "new_physics"), default="full",
+                    help="small: one mass x 24 radii of the same workload, for profiler captures; "
+                         "uneven / new_physics: the 1024-halo and 256-halo batch workloads")
     ap.add_argument("--serve-rate", type=float, default=300.0,
                     help="request rate of the serving leg (0: skip it)")
     ap.add_argument("--serve-requests", type=int, default=200)
