@@ -15,7 +15,7 @@ constexpr double kC = 299792.458;         // km/s
 constexpr double kKB = 8.617333262e-5;    // eV / K
 constexpr double kPi = 3.14159265358979323846;
 
-// Entries of the per-step coefficient table (one RK4 step = 16 values).
+// Entries of the per-step coefficient table (one RK4 step = 20 values).
 // With h = ln(1+z_end)/N, stage redshifts z_a, z_m, z_b at u = -n h, -(n+1/2) h,
 // -(n+1) h, A(z) = (1+z)^2/H, B(z) = 1/H and F(z) = G kappa (1+z) xi M_h:
 enum CoefSlot {
@@ -76,8 +76,8 @@ inline int relic_n_mass(const nu_relic& r) { return r.n_masses > 0 ? r.n_masses 
 
 // Device-visible description of one request (POD, lives in device memory).
 struct DevProblem {
-    const void* coef;       // [n_steps][16] float (mixed) or double (fp64)
-    const void* coef2;      // [n_steps][16][2] float, every value twice (mixed; packed path)
+    const void* coef;       // [n_steps][C_COUNT] float (mixed) or double (fp64)
+    const void* coef2;      // [n_steps][C_COUNT][2] float, every value twice (mixed; packed path)
     const void* x0;         // [n_radii] start radius, kpc
     const void* v0;         // [n_q] start speed, km/s
     const void* mu;         // [n_mu] cos psi

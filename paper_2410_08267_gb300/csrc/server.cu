@@ -374,7 +374,12 @@ void nu_server::run()
                 rc = NU_ETIMEDOUT;
                 break;
             }
-            if (!admit_one()) std::this_thread::sleep_for(std::chrono::microseconds(50));
+            // poll closely at first (short launches finish within a few ms and a
+            // sleep would add its granularity to every chunk), then back off
+            if (!admit_one()) {
+                if (ms_since(t_launch) < 2.0) std::this_thread::yield();
+                else std::this_thread::sleep_for(std::chrono::microseconds(50));
+            }
         }
         const double launch_ms = ms_since(t_launch);
         slot ^= 1;

@@ -280,7 +280,7 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 
 // One classical RK4 step of size -h for one trajectory (Eq. eoms in ln a).
-// c points at the step's 16 coefficients (see CoefSlot).  Every product-sum
+// c points at the step's C_COUNT coefficients (see CoefSlot).  Every product-sum
 // is an explicit fused multiply-add, so the packed two-trajectory variant
 // below performs exactly the same roundings.
 template <typename T, class Ctr>

@@ -72,18 +72,19 @@ def test_results_in_the_mix_are_bitwise_the_results_alone(chunk):
 def test_requests_joining_at_different_iterations_with_different_lengths():
     """Requests enter while others are part-way through (different progress
     and step counts in one launch) and leave at different launches."""
-    probs = _stream(12, seed=36, max_radii=16, n_steps=120)
-    probs = [pb.replace(n_steps=(60, 120, 180, 240)[i % 4]) for i, pb in enumerate(probs)]
+    probs = _stream(12, seed=36, max_radii=64, n_steps=130)
+    probs = [pb.replace(n_steps=(130, 260, 390, 520)[i % 4]) for i, pb in enumerate(probs)]
     alone = [_alone(pb)[0] for pb in probs]
     srv = nu.nu_server_create(device_bytes=512 << 20, chunk_steps=13)
     try:
         tickets = []
-        for pb in probs:
-            tickets.append(nu.nu_server_submit(srv, pb))
+        for wave in range(3):                     # three waves, a few launches apart
+            for pb in probs[4 * wave: 4 * wave + 4]:
+                tickets.append(nu.nu_server_submit(srv, pb))
             it0 = nu.nu_server_stats(srv)["iterations"]
-            t0 = time.time()                      # let at least one launch pass
-            while nu.nu_server_stats(srv)["iterations"] == it0 and time.time() - t0 < 5:
-                time.sleep(0.0005)
+            t0 = time.time()
+            while nu.nu_server_stats(srv)["iterations"] < it0 + 3 and time.time() - t0 < 5:
+                time.sleep(0.0002)
         for t, pb, a in zip(tickets, probs, alone):
             rc, out, _, _ = _wait(srv, t, pb.n_radii)
             assert rc == nu.NU_OK and np.array_equal(out, a)
