@@ -182,11 +182,60 @@ int plan_common(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* reli
 
 // Append `n` values of type T (converted from double) to a staging buffer at offset off.
 template <typename T>
-void put(std::vector<unsigned char>& buf, size_t off, const double* v, size_t n)
+void put(unsigned char* buf, size_t off, const double* v, size_t n)
 {
-    T* p = reinterpret_cast<T*>(buf.data() + off);
+    T* p = reinterpret_cast<T*>(buf + off);
     for (size_t i = 0; i < n; ++i) p[i] = (T)v[i];
 }
+
+// Page-locked host staging for the uploads of create and the reads of
+// result: one process-wide buffer that grows to the largest request, held
+// under a lock for one copy at a time (copies from page-locked memory run
+// as true DMA, without the driver's intermediate bounce).  If page-locked
+// memory cannot be had, an ordinary heap buffer is used instead.
+class Stage {
+public:
+    explicit Stage(size_t bytes) : lk_(mu())
+    {
+        Buf& b = buf();
+        if (b.cap < bytes) {
+            if (b.p) cudaFreeHost(b.p);
+            b.p = nullptr;
+            b.cap = 0;
+            const size_t want = bytes + bytes / 2;
+            if (cudaHostAlloc(reinterpret_cast<void**>(&b.p), want, cudaHostAllocPortable) == cudaSuccess)
+                b.cap = want;
+            else
+                cudaGetLastError();
+        }
+        if (b.p) {
+            p_ = b.p;
+        } else {
+            heap_.resize(bytes);
+            p_ = heap_.data();
+        }
+    }
+    unsigned char* data() { return p_; }
+
+private:
+    struct Buf {
+        unsigned char* p = nullptr;
+        size_t cap = 0;
+    };
+    static std::mutex& mu()
+    {
+        static std::mutex m;
+        return m;
+    }
+    static Buf& buf()
+    {
+        static Buf b;
+        return b;
+    }
+    std::unique_lock<std::mutex> lk_;
+    std::vector<unsigned char> heap_;
+    unsigned char* p_ = nullptr;
+};
 
 }  // namespace
 
@@ -389,10 +438,12 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     P.precision = o.precision;
     P.n_mass = nm;
 
-    std::vector<unsigned char> stage(upload_end, 0);
-    std::memcpy(stage.data() + o_prob, &P, sizeof(P));
+    Stage staging(upload_end);
+    unsigned char* stage = staging.data();
+    std::memset(stage, 0, upload_end);
+    std::memcpy(stage + o_prob, &P, sizeof(P));
     const int prefix[2] = {0, h->n_tiles};
-    std::memcpy(stage.data() + o_pref, prefix, sizeof(prefix));
+    std::memcpy(stage + o_pref, prefix, sizeof(prefix));
     if (fp64) {
         put<double>(stage, o_coef, coef.data(), coef.size());
         put<double>(stage, o_x0, x0.data(), n_radii);
@@ -401,7 +452,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
         put<double>(stage, o_smu, smu.data(), nmu);
     } else {
         put<float>(stage, o_coef, coef.data(), coef.size());
-        float* c2 = reinterpret_cast<float*>(stage.data() + o_coef2);
+        float* c2 = reinterpret_cast<float*>(stage + o_coef2);
         for (size_t i = 0; i < coef.size(); ++i) c2[2 * i] = c2[2 * i + 1] = (float)coef[i];
         put<float>(stage, o_x0, x0.data(), n_radii);
         put<float>(stage, o_v0, v0.data(), nq);
@@ -419,9 +470,9 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     }
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
-    if (cudaMemcpyAsync(base, stage.data(), upload_end, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+    if (cudaMemcpyAsync(base, stage, upload_end, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(base + o_cnt, 0, (size_t)n_radii * sizeof(unsigned), s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {   // the staging buffer is pageable and local
+        cudaStreamSynchronize(s) != cudaSuccess) {   // the staging buffer is reused after this
         cudaGetLastError();
         h->mem.release();
         return NU_ECUDA;
@@ -466,18 +517,19 @@ int nu_profile_result(nu_profile* h, double* n_over_nbar, double* err_est, int n
         return NU_ECUDA;
     }
     // out and err are adjacent in the device layout: one copy brings both back
-    std::vector<double> tmp((size_t)2 * n_radii);
+    Stage staging((size_t)2 * n_radii * sizeof(double));
+    double* tmp = reinterpret_cast<double*>(staging.data());
     const size_t stride = (size_t)(reinterpret_cast<const char*>(h->hdp.err) -
                                    reinterpret_cast<const char*>(h->hdp.out));
-    if (cudaMemcpy2D(tmp.data(), n_radii * sizeof(double), h->hdp.out, stride,
+    if (cudaMemcpy2D(tmp, n_radii * sizeof(double), h->hdp.out, stride,
                      n_radii * sizeof(double), err_est ? 2 : 1, cudaMemcpyDeviceToHost) != cudaSuccess) {
         cudaGetLastError();
         return NU_ECUDA;
     }
     for (int i = 0; i < n_radii; ++i)
         if (!std::isfinite(tmp[i])) return NU_EDEVICE;
-    std::memcpy(n_over_nbar, tmp.data(), n_radii * sizeof(double));
-    if (err_est) std::memcpy(err_est, tmp.data() + n_radii, n_radii * sizeof(double));
+    std::memcpy(n_over_nbar, tmp, n_radii * sizeof(double));
+    if (err_est) std::memcpy(err_est, tmp + n_radii, n_radii * sizeof(double));
     return NU_OK;
 }
 
@@ -604,13 +656,15 @@ int nu_batch_create(nu_profile* const* hs, int n, const nu_opts* opts, nu_batch*
     const size_t o_pref = carve((size_t)(n + 1) * sizeof(int));
     int rc = b->mem.allocate(off, o);
     if (rc != NU_OK) return rc;
-    std::vector<unsigned char> stage(off, 0);
+    Stage staging(off);
+    unsigned char* stage = staging.data();
+    std::memset(stage, 0, off);
     for (int i = 0; i < n; ++i)
-        std::memcpy(stage.data() + o_probs + i * sizeof(DevProblem), &descs[i], sizeof(DevProblem));
-    std::memcpy(stage.data() + o_pref, prefix.data(), (n + 1) * sizeof(int));
+        std::memcpy(stage + o_probs + i * sizeof(DevProblem), &descs[i], sizeof(DevProblem));
+    std::memcpy(stage + o_pref, prefix.data(), (n + 1) * sizeof(int));
     unsigned char* base = static_cast<unsigned char*>(b->mem.ptr);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
-    if (cudaMemcpyAsync(base, stage.data(), off, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+    if (cudaMemcpyAsync(base, stage, off, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         b->mem.release();
