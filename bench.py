@@ -260,13 +260,14 @@ def bench_ours(args):
 
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
-    one = W.precision_sweep(precision=W.MIXED)
+    prec = W.FP64 if args.precision == "fp64" else W.MIXED
+    one = W.precision_sweep(precision=prec)
     if args.case == "small":            # profiling case: one mass, 24 radii (fills every SM)
         one = [one[SAMPLE_MASS_INDEX].replace(radii=np.geomspace(1.0, 1000.0, 24))]
     elif args.case == "uneven":         # 1024 halos of uneven sizes in one launch
-        one = W.batched_uneven(precision=W.MIXED)
+        one = W.batched_uneven(precision=prec)
     elif args.case == "new_physics":    # 256 halos, relic kinds and couplings
-        one = W.new_physics(precision=W.MIXED)
+        one = W.new_physics(precision=prec)
     # The job at N GPUs is N copies of the workload (weak scaling); its
     # requests are partitioned over the ranks by trajectory-steps, with no
     # collective on the data path.
@@ -362,7 +363,7 @@ def bench_ours(args):
 
     # ---- the same four masses from one trajectory set (Sec. III mass reuse) ----
     reuse = None
-    if args.case == "full" and not args.main_only:
+    if args.case == "full" and not args.main_only and prec == W.MIXED:
         rpb, rms, rout = mass_reuse_once(nu, torch, stream, block, tpt, tflags,
                                          max(3, min(args.steps, 10)), flush)
         kms_main = float(np.mean(kernel_ms))
@@ -378,7 +379,7 @@ def bench_ours(args):
 
     # ---- serving: the request stream, continuous batching vs one launch per request ----
     serving = None
-    if args.serve_rate > 0 and args.case == "full" and not args.main_only:
+    if args.serve_rate > 0 and args.case == "full" and not args.main_only and prec == W.MIXED:
         n_req = args.serve_requests
         serving = {"continuous": serve_once(nu, args.serve_rate, n_req, batched=True),
                    "one_per_launch": serve_once(nu, args.serve_rate, n_req, batched=False)}
@@ -395,11 +396,20 @@ def bench_ours(args):
     flops = FLOPS_COMBINE * live_steps + sum(f * c for f, c in zip(FLOPS_EVAL, counts[:4]))
     achieved = flops / (kms / 1e3) / 1e12
     peak_mhz = clock["sm_max_mhz"] or 2070.0
-    peak = fp32_peak_tflops(peak_mhz)
+    if prec == W.FP64:
+        # FP64 mode: no unit count for GB300's FP64 pipe is at hand, so the
+        # peak is the measured FP64 FMA rate of this GPU (nu_measure_peaks)
+        peak = nu.nu_measure_peaks(stream)["dfma_tflops"]
+        peak_basis = "measured FP64 FMA rate (nu_measure_peaks)"
+    else:
+        peak = fp32_peak_tflops(peak_mhz)
+        peak_basis = f"152 SMs x 128 FP32 lanes x 2 flop/FMA x {peak_mhz:.0f} MHz"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC_BYTES.get(f"{block}x{tpt}{'xg' if tflags else ''}"),
-                "kernel": f"traj_kernel<float,{min(tpt, 2)},packed={tpt == 3},l1_table={bool(tflags)}>",
+                "traffic": (NCU_TRAFFIC_BYTES.get(f"{block}x{tpt}{'xg' if tflags else ''}")
+                            if args.case == "full" and prec == W.MIXED else None),
+                "kernel": (f"traj_kernel<{'double' if prec == W.FP64 else 'float'},{min(tpt, 2)},"
+                           f"packed={tpt == 3},l1_table={bool(tflags)}>"),
                 "kernel_ms": kms,
                 "flops_per_launch": flops, "flops_per_executed_traj_step": flops / live_steps,
                 "executed_traj_steps": live_steps,
@@ -407,7 +417,7 @@ def bench_ours(args):
                 "branch_counts": {"beyond_R": counts[0], "shell": counts[1],
                                   "nfw_poly": counts[2], "nfw_log": counts[3]},
                 "full_eval_equiv_tflops": FLOPS_FULL * traj_steps / (kms / 1e3) / 1e12,
-                "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop/FMA x {peak_mhz:.0f} MHz"}
+                "peak_basis": peak_basis}
 
     # ---- CPU baseline: the oracle on a bounded sample, and the accuracy check ----
     full = W.precision_sweep(precision=W.MIXED)
@@ -439,9 +449,12 @@ def bench_ours(args):
         WORKLOAD_USED = WORKLOAD
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_USED, "traj_steps_per_step": job_traj_steps,
-                       "precision": "mixed: FP32 state/force, FP64 tables and sums",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == W.FP64 else "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_USED + (" (FP64 mode)" if prec == W.FP64 else ""),
+                       "traj_steps_per_step": job_traj_steps,
+                       "precision": ("FP64 state, force, f and sums" if prec == W.FP64 else
+                                     "mixed: FP32 state/force, FP64 tables and sums"),
                        "l2": "flushed (256 MiB write) between timed steps",
                        "launch": f"one persistent batched launch per step: grid {grid} CTAs x {block} "
                                  f"threads, shape {block}x{tpt}{'xg' if tflags else ''} "
@@ -491,6 +504,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=300.0,
                     help="request rate of the serving leg (0: skip it)")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed",
+                    help="fp64: the verification mode (FP64 state and force)")
     ap.add_argument("--main-only", action="store_true",
                     help="skip the serving and mass-reuse legs (profiler runs)")
     ap.add_argument("--serve-sweep", action="store_true",

@@ -449,6 +449,7 @@ typedef struct nu_peaks {
     double lg2_gops;
     int sm_count;
     int clock_mhz_nominal;   /* cudaDevAttrClockRate / 1000 */
+    double dfma_tflops;      /* FP64 fused multiply-add (the FP64 mode's ALU peak) */
 } nu_peaks;
 NU_API int nu_measure_peaks(void* stream, nu_peaks* out);
 

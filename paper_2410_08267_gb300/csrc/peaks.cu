@@ -1,7 +1,7 @@
 // Arithmetic-throughput microbenchmarks of the GPU, used as the measured
 // roofline denominators of the trajectory kernel (an FP32 ALU-bound path):
-// scalar FP32 FMA, packed FP32x2 FMA, and the special-function unit's
-// reciprocal square root and base-2 logarithm.  Every thread runs 8
+// scalar FP32 FMA, packed FP32x2 FMA, the special-function unit's reciprocal
+// square root and base-2 logarithm, and FP64 FMA (for the FP64 mode).  Every thread runs 8
 // independent dependency chains so that the pipes, not latency, bound the
 // rate; the grid fills every SM several times over.
 #include <cuda_runtime.h>
@@ -53,6 +53,21 @@ __global__ void __launch_bounds__(kBlock) ffma2_kernel(float* out, float a, floa
         s += f.x + f.y;
     }
     if (s == 1.2345f) out[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kBlock) dfma_kernel(float* out, double a, double b, int iters)
+{
+    double v[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) v[c] = threadIdx.x * 1e-3 + c;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) v[c] = fma(v[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += v[c];
+    if (s == 1.2345) out[blockIdx.x] = (float)s;
 }
 
 __global__ void __launch_bounds__(kBlock) rsqrt_kernel(float* out)
@@ -110,16 +125,17 @@ extern "C" int nu_measure_peaks(void* stream, nu_peaks* out)
         if (sink) cudaFree(sink);
         return NU_ECUDA;
     }
-    float ms[4] = {0, 0, 0, 0};
+    float ms[5] = {0, 0, 0, 0, 0};
     int rc = NU_OK;
-    for (int which = 0; which < 4 && rc == NU_OK; ++which) {
+    for (int which = 0; which < 5 && rc == NU_OK; ++which) {
         for (int rep = 0; rep < 2 && rc == NU_OK; ++rep) {   // first pass warms up
             cudaEventRecord(e0, s);
             switch (which) {
             case 0: ffma_kernel<<<grid, kBlock, 0, s>>>(sink, 0.999f, 1e-3f); break;
             case 1: ffma2_kernel<<<grid, kBlock, 0, s>>>(sink, 0.999f, 1e-3f); break;
             case 2: rsqrt_kernel<<<grid, kBlock, 0, s>>>(sink); break;
-            default: lg2_kernel<<<grid, kBlock, 0, s>>>(sink); break;
+            case 3: lg2_kernel<<<grid, kBlock, 0, s>>>(sink); break;
+            default: dfma_kernel<<<grid, kBlock, 0, s>>>(sink, 0.999, 1e-3, kIters / 16); break;
             }
             count_launch();
             cudaEventRecord(e1, s);
@@ -141,6 +157,7 @@ extern "C" int nu_measure_peaks(void* stream, nu_peaks* out)
     out->ffma2_tflops = 4.0 * ops / (ms[1] * 1e-3) / 1e12;
     out->rsqrt_gops = ops / (ms[2] * 1e-3) / 1e9;
     out->lg2_gops = ops / (ms[3] * 1e-3) / 1e9;
+    out->dfma_tflops = 2.0 * ops / 16.0 / (ms[4] * 1e-3) / 1e12;   // a sixteenth of the iterations
     out->sm_count = sms;
     out->clock_mhz_nominal = clk / 1000;
     return NU_OK;

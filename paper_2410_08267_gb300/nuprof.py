@@ -97,7 +97,7 @@ class nu_serve_stats(C.Structure):
 class nu_peaks(C.Structure):
     _fields_ = [("ffma_tflops", C.c_double), ("ffma2_tflops", C.c_double),
                 ("rsqrt_gops", C.c_double), ("lg2_gops", C.c_double),
-                ("sm_count", C.c_int), ("clock_mhz_nominal", C.c_int)]
+                ("sm_count", C.c_int), ("clock_mhz_nominal", C.c_int), ("dfma_tflops", C.c_double)]
 
 
 class nu_tune_result(C.Structure):

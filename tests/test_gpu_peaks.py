@@ -17,3 +17,4 @@ def test_measured_peaks_are_plausible():
     for k in ("ffma_tflops", "ffma2_tflops"):
         assert 0.2 * nominal < p[k] < 2.5 * nominal, (k, p[k], nominal)
     assert p["rsqrt_gops"] > 0 and p["lg2_gops"] > 0
+    assert 0 < p["dfma_tflops"] < p["ffma_tflops"]
