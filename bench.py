@@ -226,7 +226,7 @@ def serve_once(nu, rate, n_requests, seed=2412, batched=True, chunk=100, budget=
     """The serving workload (Poisson arrivals, mixed requests) through the
     continuous-batching server, or through its one-request-per-launch form."""
     reqs = W.serving_stream(rate=rate, n_requests=n_requests, seed=seed)
-    srv = (nu.nu_server_create(device_bytes=budget, chunk_steps=chunk, max_active=256) if batched
+    srv = (nu.nu_server_create(device_bytes=budget, chunk_steps=chunk, max_active=64) if batched
            else nu.nu_server_create(device_bytes=budget, chunk_steps=0, max_active=1))
     try:
         wall, lat, failed = drive_stream(nu, srv, reqs)

@@ -351,7 +351,9 @@ NU_API int nu_batch_info(const nu_batch* b, int* n_tiles, long long* traj_steps,
 typedef struct nu_server nu_server;
 typedef struct nu_server_opts {
     size_t device_bytes;     /* device memory budget of the server (>= 1 MiB)     */
-    int max_active;          /* requests on the GPU at once (0 -> 1024)           */
+    int max_active;          /* requests on the GPU at once (0 -> 64: beyond that,
+                                sharing launches among more requests only slows
+                                each one down)                                  */
     int chunk_steps;         /* RK4 steps per launch (0: a request's whole run)   */
     int precision;           /* NU_FP64 or NU_MIXED: every request uses it        */
     int block, tpt, flags;   /* launch shape (0: 128 x 3 with NU_FLAG_GTAB for mixed,

@@ -443,7 +443,7 @@ int nu_server_create(const nu_server_opts* opts, nu_server** out)
     s->o = *opts;
     nu_server_opts& o = s->o;
     if (o.precision != NU_FP64 && o.precision != NU_MIXED) return NU_EINVAL;
-    if (o.max_active <= 0) o.max_active = 1024;
+    if (o.max_active <= 0) o.max_active = 64;
     if (o.max_active > 65536) return NU_EINVAL;
     if (o.block == 0) o.block = o.precision == NU_MIXED ? 128 : 256;
     if (o.tpt == 0) {
