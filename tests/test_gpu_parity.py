@@ -213,3 +213,28 @@ def test_rays_that_miss_the_halo_stop_at_once(prec):
         nu.nu_batch_destroy(b)
         nu.nu_profile_destroy(h)
     assert live_far < 0.6 * pb.traj_steps, (live_far, pb.traj_steps)
+
+
+@pytest.mark.parametrize("prec, steps, tpt", [(W.MIXED, nu.NU_MAX_STEPS, 3), (W.MIXED, nu.NU_MAX_STEPS, 1),
+                                              (W.FP64, 2000, 1)])
+def test_tables_too_large_for_shared_memory_are_read_through_l1(prec, steps, tpt):
+    """The longest runs: a coefficient table above 227 KB cannot be staged in
+    shared memory and is read through L1 instead, with the same results as
+    the L1 table flag gives."""
+    pb = W.plain_small(precision=prec)[0].replace(n_steps=steps, n_q=16, n_mu=8)
+    outs = []
+    for flags in (0, nu.NU_FLAG_GTAB):
+        h = nu.create(pb, block=128, tpt=tpt)
+        o = nu.nu_opts()
+        o.flags = flags
+        b = nu.nu_batch_create([h], o)
+        try:
+            nu.nu_batch_run(b)
+            outs.append(nu.nu_profile_result(h, pb.n_radii)[0])
+        finally:
+            nu.nu_batch_destroy(b)
+            nu.nu_profile_destroy(h)
+    assert np.all(np.isfinite(outs[0])) and np.array_equal(outs[0], outs[1])
+    # the outer radii are well conditioned: the oracle agrees at the stated tolerance
+    ref = oracle.profile(pb, radius_sel=[8, 9])
+    assert np.all(rel_err(outs[0][8:], ref[8:]) < (TOL_FP64 if prec == W.FP64 else TOL_MIXED))
