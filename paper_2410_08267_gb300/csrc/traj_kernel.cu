@@ -97,7 +97,7 @@ __device__ __forceinline__ double nfw_I(double y)
     const double t = y / (1.0 + y);
     if (t < 0.5) {
         double p = 1.0 / 52.0;
-#pragma unroll 10
+#pragma unroll   // fully: the coefficients 1/(k+2) become compile-time constants
         for (int k = 49; k >= 0; --k) p = fma(p, t, 1.0 / (double)(k + 2));
         return (t * t) * p;
     }
