@@ -109,11 +109,11 @@ extern "C" {
 #define NU_FLAG_GRAPH    2 /* batches: capture the launch in a CUDA graph      */
 #define NU_FLAG_TIMING   4 /* batches: record CUDA events around the trajectory
                               kernel (read with nu_batch_kernel_ms)            */
-#define NU_FLAG_GTAB     8 /* batches: read the per-step coefficient table in
-                              place through the L1 cache instead of staging it
-                              in shared memory (frees shared memory, so more
-                              CTAs fit on an SM); results are identical.  A
-                              table larger than 227 KB is always read this way */
+#define NU_FLAG_GTAB     8 /* runs and batches: read the per-step coefficient
+                              table in place through the L1 cache instead of
+                              staging it in shared memory (frees shared memory,
+                              so more CTAs fit on an SM); results are identical.
+                              A table larger than 227 KB is always read this way */
 
 typedef struct nu_cosmo {
     double Om;       /* matter density today; Omega_Lambda = 1 - Om (Sec. II.A) */

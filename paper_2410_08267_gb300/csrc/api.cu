@@ -489,14 +489,16 @@ int nu_profile_run(nu_profile* h, void* stream)
     if (!h) return NU_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int grid = 0;
-    int rc = persistent_grid(h->opts.precision, h->opts.tpt, h->opts.block, h->smem, h->n_tiles, &grid);
+    const bool gtab = (h->opts.flags & NU_FLAG_GTAB) != 0;
+    int rc = persistent_grid(h->opts.precision, h->opts.tpt, h->opts.block, h->smem, h->n_tiles, &grid,
+                             gtab);
     if (rc != NU_OK) return rc;
     if (cudaMemsetAsync(h->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess) {
         cudaGetLastError();
         return NU_ECUDA;
     }
     rc = launch_traj(h->opts.precision, h->opts.tpt, h->opts.block, grid, h->smem, h->d_prob,
-                     h->d_prefix, 1, h->n_tiles, h->d_ctrl, stream);
+                     h->d_prefix, 1, h->n_tiles, h->d_ctrl, stream, gtab);
     if (rc != NU_OK) return rc;
     auto ev = std::make_shared<RunEvent>();
     if (!ev->ev || cudaEventRecord(ev->ev, s) != cudaSuccess) {

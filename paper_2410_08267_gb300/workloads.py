@@ -133,6 +133,20 @@ def precision_sweep_reuse(precision: int = MIXED, masses=PRECISION_SWEEP_MASSES,
                    masses=tuple(masses))
 
 
+def paper_production_grid(precision: int = MIXED, n_steps: int = 800) -> Problem:
+    """The production grid of Sec. III as one mass-reuse request: 20 radii
+    log 10 kpc - 50 Mpc, 200 momenta log 0.01-400 k_B T0 for the fiducial
+    0.3 eV relic, 10 directions (Gauss-Legendre on [-1, 1] here) and 15 masses
+    linear in 0.01-0.5 eV read from one trajectory set; a 1e12 Msun halo with
+    the c-M law and linear growth, integrated back to z_i.  The step count is
+    not stated in the paper (800 here)."""
+    M = 1e12
+    return Problem(M_h=M, c=c_of_M(M), xi_kind=XI_LINEAR, xi_p=(1.0, 0.0, 0.0), m_eV=0.3,
+                   radii=np.geomspace(10.0, 50000.0, 20), n_q=200, q_min=0.01, q_max=400.0,
+                   n_mu=10, n_steps=n_steps, z_end=0.0, precision=precision,
+                   masses=tuple(float(m) for m in np.linspace(0.01, 0.5, 15)))
+
+
 def batched_uneven(n_halos: int = 1024, seed: int = 2410, precision: int = MIXED,
                    n_steps: int = 400) -> List[Problem]:
     """1024 halos: log10 M ~ U[11,15], c lognormal (0.15 dex) about the c-M law,

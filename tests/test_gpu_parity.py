@@ -238,3 +238,10 @@ def test_tables_too_large_for_shared_memory_are_read_through_l1(prec, steps, tpt
     # the outer radii are well conditioned: the oracle agrees at the stated tolerance
     ref = oracle.profile(pb, radius_sel=[8, 9])
     assert np.all(rel_err(outs[0][8:], ref[8:]) < (TOL_FP64 if prec == W.FP64 else TOL_MIXED))
+
+
+def test_single_run_with_the_table_through_l1_is_bitwise_the_staged_run():
+    pb = W.plain_small(precision=W.MIXED)[0]
+    staged = nu.profile(pb, block=128, tpt=3)[0]
+    l1 = nu.profile(pb, block=128, tpt=3, flags=nu.NU_FLAG_GTAB)[0]
+    assert np.array_equal(staged, l1)
