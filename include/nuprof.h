@@ -376,6 +376,7 @@ typedef struct nu_serve_stats {
     int pending, active, max_active_seen;
     int status;              /* NU_OK, or the error that stopped the server        */
     long long arena_bytes, arena_peak;
+    long long early;         /* results delivered while their last launch still ran */
 } nu_serve_stats;
 
 /* Start a server on the current device.  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */

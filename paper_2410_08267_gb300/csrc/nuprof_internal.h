@@ -113,6 +113,11 @@ struct DevProblem {
     // means n_steps (a whole run).
     void* state;
     int step_begin, step_end;
+    // Early completion signal (serving): when set, the CTA that finishes the
+    // last radius of the request writes 1 to done_flag (host-mapped memory)
+    // after counting the radii in done_count (zeroed before the launch).
+    unsigned* done_count;
+    volatile unsigned* done_flag;
 };
 
 // Accessors used by the request server (api.cu).

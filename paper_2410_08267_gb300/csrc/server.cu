@@ -14,6 +14,10 @@
 // with the same operations and the same tiles whatever shares its launches,
 // its result is bitwise the one it gets alone.
 //
+// A request whose last chunk runs in a launch is delivered as soon as its
+// last radius is finished: the kernel raises a flag in host-mapped memory and
+// the worker reads the result while the launch still runs the others.
+//
 // Every wait on the GPU is bounded (gpu_timeout_ms): a launch that does not
 // complete in time fails the requests it carried with NU_ETIMEDOUT and the
 // server stops admitting work.
@@ -175,7 +179,7 @@ struct nu_server {
 
     // statistics (under mu)
     long long submitted = 0, admitted = 0, completed = 0, cancelled = 0, rejected = 0;
-    long long iterations = 0, traj_steps = 0;
+    long long iterations = 0, traj_steps = 0, early = 0;
     double busy_ms = 0.0;
     int max_active_seen = 0;
     std::vector<double> latencies;
@@ -190,18 +194,37 @@ struct nu_server {
         return w;
     }
     void finish(Active& a, int rc, std::vector<double>* out, std::vector<double>* err);
+    void release(Active& a);                // memory back to the arena
+    void record(Active& a, int rc, std::vector<double>* out, std::vector<double>* err);
+
+    // early delivery: a request whose last chunk is in the launch signals its
+    // last radius through host-mapped flags, and its result is read and
+    // delivered while the launch still runs the others
+    unsigned* h_flags = nullptr;            // page-locked, mapped: one per active slot
+    unsigned* d_flags = nullptr;            // the same memory as the device sees it
+    unsigned* d_counts = nullptr;           // radii finished, per active slot (arena)
 };
 
 void nu_server::finish(Active& a, int rc, std::vector<double>* out, std::vector<double>* err)
+{
+    release(a);
+    record(a, rc, out, err);
+}
+
+void nu_server::release(Active& a)
+{
+    nu_profile_destroy(a.h);                 // returns its memory to the arena
+    arena.release(a.state);
+    on_device.fetch_sub(1);
+}
+
+void nu_server::record(Active& a, int rc, std::vector<double>* out, std::vector<double>* err)
 {
     Done d;
     d.rc = rc;
     if (out) d.out.swap(*out);
     if (err) d.err.swap(*err);
     d.latency_ms = ms_since(a.t_submit);
-    nu_profile_destroy(a.h);                 // returns its memory to the arena
-    arena.release(a.state);
-    on_device.fetch_sub(1);
     std::lock_guard<std::mutex> g(mu);
     if (rc == NU_OK) {
         ++completed;
@@ -323,6 +346,7 @@ void nu_server::run()
         if (chunk > 0 && traj_active * chunk > o.step_budget)
             chunk = std::max(1, (int)(o.step_budget / traj_active));
         std::vector<DevProblem> desc(active.size());
+        std::vector<int> early_st(active.size(), 0);   // 1: signals this launch, 2: delivered
         std::vector<int> prefix(active.size() + 1, 0);
         long long steps_this = 0;
         size_t smem = 0;                          // the largest table staged this launch
@@ -336,6 +360,14 @@ void nu_server::run()
             d.state = a.state;
             d.step_begin = a.progress;
             d.step_end = std::min(a.n_steps, a.progress + (chunk > 0 ? chunk : a.n_steps));
+            d.done_count = nullptr;
+            d.done_flag = nullptr;
+            if (h_flags && d.step_end == a.n_steps) {
+                h_flags[i] = 0u;
+                d.done_count = d_counts + i;
+                d.done_flag = d_flags + i;
+                early_st[i] = 1;
+            }
             desc[i] = d;
             prefix[i + 1] = prefix[i] + d.tiles_per_seg * d.n_radii;
             steps_this += profile_n_traj(a.h) * (d.step_end - d.step_begin);
@@ -346,7 +378,8 @@ void nu_server::run()
                             compute) != cudaSuccess ||
             cudaMemcpyAsync(d_prefix[slot], prefix.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice,
                             compute) != cudaSuccess ||
-            cudaMemsetAsync(d_ctrl, 0, 2 * sizeof(unsigned), compute) != cudaSuccess)
+            cudaMemsetAsync(d_ctrl, 0, 2 * sizeof(unsigned), compute) != cudaSuccess ||
+            (h_flags && cudaMemsetAsync(d_counts, 0, n * sizeof(unsigned), compute) != cudaSuccess))
             rc = NU_ECUDA;
         int grid = 0, per_sm = 0, sms = 0;
         if (rc == NU_OK) rc = max_ctas_per_sm(o.precision, tpt, o.block, smem, &per_sm, gtab);
@@ -374,6 +407,17 @@ void nu_server::run()
                 rc = NU_ETIMEDOUT;
                 break;
             }
+            // deliver requests that have finished inside the running launch
+            for (int i = 0; i < n; ++i) {
+                if (early_st[i] != 1 || reinterpret_cast<volatile unsigned*>(h_flags)[i] != 1u) continue;
+                const int nr = profile_n_out(active[i].h);
+                std::vector<double> out(nr), err(nr);
+                const int r = profile_read(active[i].h, out.data(), err.data(), upload);
+                record(active[i], r, &out, &err);
+                early_st[i] = 2;
+                std::lock_guard<std::mutex> g(mu);
+                ++early;
+            }
             // poll closely at first (short launches finish within a few ms and a
             // sleep would add its granularity to every chunk), then back off
             if (!admit_one()) {
@@ -396,13 +440,17 @@ void nu_server::run()
                 // the GPU may still be running the launch: fail the requests but
                 // keep their memory (it may still be written)
                 std::lock_guard<std::mutex> g(mu);
-                for (auto& a : active) done[a.ticket] = Done{rc, {}, {}, ms_since(a.t_submit)};
+                for (size_t i = 0; i < active.size(); ++i)   // (those delivered early keep their result)
+                    if (early_st[i] != 2) done[active[i].ticket] = Done{rc, {}, {}, ms_since(active[i].t_submit)};
                 for (auto& a : staged) done[a.ticket] = Done{rc, {}, {}, ms_since(a.t_submit)};
                 active.clear();
                 staged.clear();
                 return;
             }
-            for (auto& a : active) finish(a, rc, nullptr, nullptr);
+            for (size_t i = 0; i < active.size(); ++i) {
+                if (early_st[i] == 2) release(active[i]);
+                else finish(active[i], rc, nullptr, nullptr);
+            }
             active.clear();
             continue;
         }
@@ -422,6 +470,10 @@ void nu_server::run()
             a.progress = desc[i].step_end;
             if (a.progress < a.n_steps) {
                 keep.push_back(a);
+                continue;
+            }
+            if (early_st[i] == 2) {               // delivered during the launch
+                release(a);
                 continue;
             }
             const int nr = profile_n_out(a.h);
@@ -474,6 +526,7 @@ int nu_server_create(const nu_server_opts* opts, nu_server** out)
         s->d_prefix[i] = static_cast<int*>(s->arena.alloc((size_t)(o.max_active + 1) * sizeof(int)));
     }
     s->d_ctrl = static_cast<unsigned*>(s->arena.alloc(256));
+    s->d_counts = static_cast<unsigned*>(s->arena.alloc((size_t)o.max_active * sizeof(unsigned)));
     s->capacity = s->arena.size() - s->arena.used();
     auto fail = [&](int rc) {
         if (s->compute) cudaStreamDestroy(s->compute);
@@ -486,12 +539,24 @@ int nu_server_create(const nu_server_opts* opts, nu_server** out)
         }
         return rc;
     };
-    if (!s->d_desc[0] || !s->d_desc[1] || !s->d_prefix[0] || !s->d_prefix[1] || !s->d_ctrl)
+    if (!s->d_desc[0] || !s->d_desc[1] || !s->d_prefix[0] || !s->d_prefix[1] || !s->d_ctrl ||
+        !s->d_counts)
         return fail(NU_ENOMEM);
+    // completion flags in page-locked memory the GPU writes directly; without
+    // them results are delivered when their launch ends
+    if (cudaHostAlloc(reinterpret_cast<void**>(&s->h_flags), (size_t)o.max_active * sizeof(unsigned),
+                      cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_flags), s->h_flags, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->h_flags) cudaFreeHost(s->h_flags);
+        s->h_flags = nullptr;
+        s->d_flags = nullptr;
+    }
     if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        if (s->h_flags) cudaFreeHost(s->h_flags);
         return fail(NU_ECUDA);
     }
     nu_server* raw = s.get();
@@ -600,6 +665,7 @@ int nu_server_stats(nu_server* s, nu_serve_stats* out)
     out->arena_bytes = (long long)s->arena.size();
     out->arena_peak = (long long)s->arena.peak();
     out->status = s->fatal;
+    out->early = s->early;
     if (!s->latencies.empty()) {
         std::vector<double> l = s->latencies;
         std::sort(l.begin(), l.end());
@@ -637,9 +703,10 @@ void nu_server_destroy(nu_server* s)
                 s->arena.release(a.state);
             }
     }
-    // after a timeout the arena may still be in use by the GPU: it is leaked
-    // rather than freed under a running kernel
+    // after a timeout the arena and the flags may still be in use by the GPU:
+    // they are leaked rather than freed under a running kernel
     if (gpu_ok) {
+        if (s->h_flags) cudaFreeHost(s->h_flags);
         if (s->o.alloc) {
             if (s->o.free) s->o.free(s->block, s->o.device_bytes, s->o.alloc_ctx);
         } else {

@@ -726,7 +726,16 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                     if (!isfinite(ratio)) atomicOr(P.status, 1);
                 }
             }
-            if (lane == 0) P.seg_count[seg] = 0u;   // ready for the next run
+            if (lane == 0) {
+                P.seg_count[seg] = 0u;              // ready for the next run
+                if (P.done_flag) {                  // serving: signal the request's last radius
+                    __threadfence_system();
+                    if (atomicAdd(P.done_count, 1u) == (unsigned)P.n_radii - 1u) {
+                        __threadfence_system();
+                        *P.done_flag = 1u;
+                    }
+                }
+            }
         }
         // the next iteration's first __syncthreads orders s_tile/s_last reuse
     }

@@ -91,7 +91,7 @@ class nu_serve_stats(C.Structure):
                 ("traj_steps", C.c_longlong), ("busy_ms", C.c_double), ("p50_ms", C.c_double),
                 ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("pending", C.c_int),
                 ("active", C.c_int), ("max_active_seen", C.c_int), ("status", C.c_int),
-                ("arena_bytes", C.c_longlong), ("arena_peak", C.c_longlong)]
+                ("arena_bytes", C.c_longlong), ("arena_peak", C.c_longlong), ("early", C.c_longlong)]
 
 
 class nu_peaks(C.Structure):

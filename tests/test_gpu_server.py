@@ -191,3 +191,23 @@ def test_launch_over_its_time_limit_fails_requests_and_stops_the_server():
     torch.cuda.synchronize()
     out, _ = nu.profile(probs[0].replace(n_steps=50))
     assert np.all(np.isfinite(out))
+
+
+def test_requests_finished_inside_a_launch_are_delivered_before_it_ends():
+    """A small request that shares a launch with a large one is delivered as
+    soon as its own radii are done (through a flag the kernel raises in
+    host-mapped memory), with the same bits as alone."""
+    big = _stream(1, seed=41, max_radii=256, n_steps=400)[0].replace(n_q=256, n_mu=64)
+    small = [pb.replace(n_steps=400) for pb in _stream(3, seed=42, max_radii=8, n_steps=400)]
+    probs = [big] + small
+    alone = [_alone(pb)[0] for pb in probs]
+    srv = nu.nu_server_create(device_bytes=1 << 30, chunk_steps=0)
+    try:
+        tickets = [nu.nu_server_submit(srv, pb) for pb in probs]
+        res = [_wait(srv, t, pb.n_radii) for t, pb in zip(tickets, probs)]
+        for (rc, out, _, _), a in zip(res, alone):
+            assert rc == nu.NU_OK and np.array_equal(out, a)
+        st = nu.nu_server_stats(srv)
+        assert st["early"] >= 1, st
+    finally:
+        nu.nu_server_destroy(srv)
