@@ -211,3 +211,20 @@ def test_requests_finished_inside_a_launch_are_delivered_before_it_ends():
         assert st["early"] >= 1, st
     finally:
         nu.nu_server_destroy(srv)
+
+
+def test_served_profiles_match_the_oracle():
+    """The metric's accuracy bar for served profiles: each result against the
+    FP64 oracle (conditioning-aware, 1e-4 in mixed precision) on sampled radii."""
+    from gpu_common import assert_parity
+    probs = [pb.replace(n_q=32, n_mu=12) for pb in _stream(4, seed=43, max_radii=12, n_steps=400)]
+    srv = nu.nu_server_create(device_bytes=256 << 20, chunk_steps=100)
+    try:
+        tickets = [nu.nu_server_submit(srv, pb) for pb in probs]
+        for t, pb in zip(tickets, probs):
+            rc, out, _, _ = _wait(srv, t, pb.n_radii)
+            assert rc == nu.NU_OK
+            sel = sorted({0, pb.n_radii // 2, pb.n_radii - 1})
+            assert_parity(out, pb, sel=sel, where="served")
+    finally:
+        nu.nu_server_destroy(srv)
