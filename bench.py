@@ -245,9 +245,12 @@ def paper_grid_once(nu, torch, stream, reps=10):
                                 "the C version 'a few seconds' per mass on a laptop CPU")}
 
 
-def serve_once(nu, rate, n_requests, seed=2412, batched=True, chunk=100, budget=8 << 30):
+def serve_once(nu, rate, n_requests, seed=2412, batched=True, chunk=0, budget=8 << 30):
     """The serving workload (Poisson arrivals, mixed requests) through the
-    continuous-batching server, or through its one-request-per-launch form."""
+    continuous-batching server, or through its one-request-per-launch form.
+    chunk 0: whole runs, requests join at the next launch; chunk > 0: each
+    launch advances every request by that many steps, so requests also join
+    ones already part-way through."""
     reqs = W.serving_stream(rate=rate, n_requests=n_requests, seed=seed)
     srv = (nu.nu_server_create(device_bytes=budget, chunk_steps=chunk, max_active=64) if batched
            else nu.nu_server_create(device_bytes=budget, chunk_steps=0, max_active=1))
@@ -257,7 +260,9 @@ def serve_once(nu, rate, n_requests, seed=2412, batched=True, chunk=100, budget=
     finally:
         nu.nu_server_destroy(srv)
     lat = np.asarray(lat)
-    return {"rate_per_s": rate, "requests": n_requests, "mode": "continuous" if batched else "one_per_launch",
+    mode = ("one_per_launch" if not batched else
+            "continuous" if chunk == 0 else f"continuous_chunk{chunk}")
+    return {"rate_per_s": rate, "requests": n_requests, "mode": mode,
             "profiles_per_s": len(lat) / wall, "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None, "failed": failed,
             "launches": st["iterations"], "max_active": st["max_active_seen"],
@@ -410,6 +415,8 @@ def bench_ours(args):
     if args.serve_rate > 0 and args.case == "full" and not args.main_only and prec == W.MIXED:
         n_req = args.serve_requests
         serving = {"continuous": serve_once(nu, args.serve_rate, n_req, batched=True),
+                   "continuous_chunk100": serve_once(nu, args.serve_rate, n_req, batched=True,
+                                                     chunk=100),
                    "one_per_launch": serve_once(nu, args.serve_rate, n_req, batched=False)}
 
     if dist is not None:
@@ -512,8 +519,8 @@ def bench_serve_sweep(args):
     from paper_2410_08267_gb300 import nuprof as nu
     for rate in (10, 30, 100, 300, 1000, 3000, 5000):
         n_req = int(min(args.serve_requests, max(20, rate * 2)))
-        for batched in (True, False):
-            r = serve_once(nu, rate, n_req, batched=batched)
+        for batched, chunk in ((True, 0), (True, 100), (False, 0)):
+            r = serve_once(nu, rate, n_req, batched=batched, chunk=chunk)
             print(json.dumps({"metric": "served profiles/s", **r}), flush=True)
     return 0
 
