@@ -107,3 +107,17 @@ def test_mass_reuse_through_the_server():
         assert np.array_equal(res[t2][1], alone.reshape(4, -1)[3])   # fiducial row
     finally:
         nu.nu_server_destroy(srv)
+
+
+def test_the_largest_mass_list():
+    """NU_MAX_MASSES masses from one trajectory set: every row against the
+    oracle's mass-reuse form on the outermost radius, the fiducial row bitwise
+    the one-mass request."""
+    pb = W.plain_small(precision=W.FP64)[0].replace(n_q=40, q_max=100.0, n_mu=8, n_steps=200,
+                                                     m_eV=0.3)
+    masses = tuple(float(m) for m in np.linspace(0.01, 0.6, nu.NU_MAX_MASSES - 1)) + (pb.m_eV,)
+    got = _run(pb.replace(masses=masses))[0]
+    assert got.shape == (nu.NU_MAX_MASSES, pb.n_radii) and np.all(np.isfinite(got))
+    assert np.array_equal(got[-1], _run(pb)[0][0])
+    ref = oracle.profile_masses(pb, masses, radius_sel=[pb.n_radii - 1])
+    assert np.all(rel_err(got[:, -1], ref[:, -1]) < TOL[W.FP64])
