@@ -28,6 +28,7 @@ NU_RADII_KPC, NU_RADII_R200 = 0, 1
 NU_FLAG_KEEP_QI, NU_FLAG_GRAPH, NU_FLAG_TIMING, NU_FLAG_GTAB = 1, 2, 4, 8
 NU_MAX_STEPS = 3000
 NU_MAX_MASSES = 64
+NU_MAX_FTABLE = 4096
 
 
 class NuError(RuntimeError):

@@ -73,3 +73,15 @@ def test_table_through_batch_and_server_is_bitwise_alone():
         nu.nu_batch_destroy(b)
         for h in hs:
             nu.nu_profile_destroy(h)
+
+
+@pytest.mark.parametrize("n_table", [2, nu.NU_MAX_FTABLE])
+def test_table_sizes_at_the_limits(n_table):
+    """The smallest (2 nodes) and largest tables, against the oracle's own
+    evaluation of the same tabulated f."""
+    q = np.geomspace(1e-3, 40.0, n_table)
+    tab = tuple(float(v) for v in 1.0 / (1.0 + np.exp(q)))
+    pb = _base(W.FP64).replace(f_kind=W.F_TABLE, f_p=(1e-3, 40.0), f_table=tab, n_steps=150)
+    got = nu.profile(pb)[0]
+    assert np.all(np.isfinite(got))
+    assert_parity(got, pb, sel=[0, pb.n_radii - 1], where=f"{n_table}-node table")
