@@ -62,6 +62,10 @@ SMS, FP32_LANES_PER_SM = 152, 128
 # profiles/traj_kernel_precision_sweep_mixed.md.  Must be reset to None
 # whenever the kernel changes, until it is captured again.
 NCU_TRAFFIC_BYTES = {"128x3xg": 697984.0}
+# Pipe utilisation of the same kernel and shape on this workload, from one-pass
+# ncu captures (sm__pipe_fma_cycles_active, smsp__issue_active), also recorded
+# in that profile summary; reset together with the traffic when the kernel changes.
+NCU_PIPES = {"128x3xg": {"fma_pipe_cycles_active": 0.662, "issue_slots_active": 0.627}}
 SAMPLE_RADII = (0, 9, 18, 27, 36, 45, 54, 63)   # oracle sample: ~1 s on 16 cores
 SAMPLE_MASS_INDEX = 2          # 0.1 eV
 
@@ -443,6 +447,8 @@ def bench_ours(args):
                 "frac": achieved / peak,
                 "traffic": (NCU_TRAFFIC_BYTES.get(f"{block}x{tpt}{'xg' if tflags else ''}")
                             if args.case == "full" and prec == W.MIXED else None),
+                "ncu_pipes": (NCU_PIPES.get(f"{block}x{tpt}{'xg' if tflags else ''}")
+                              if args.case == "full" and prec == W.MIXED else None),
                 "kernel": (f"traj_kernel<{'double' if prec == W.FP64 else 'float'},{min(tpt, 2)},"
                            f"packed={tpt == 3},l1_table={bool(tflags)}>"),
                 "kernel_ms": kms,
