@@ -508,7 +508,9 @@ def bench_ours(args):
             "e2e": {"value": job_traj_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d * world,
                     "d2h_bytes_per_step": d2h * world,
                     "path": "create (host tables -> device) + batch + run + result + destroy"},
-            "gpu_launches": launches, "wall_s": wall, "serving": serving, "mass_reuse": reuse, "paper_grid": paper_grid,
+            "gpu_launches": launches, "wall_s": wall,
+            "step_ms": {"mean": ms_per_step, "median": float(np.median(step_ms)),
+                        "min": float(np.min(step_ms)), "max": float(np.max(step_ms))}, "serving": serving, "mass_reuse": reuse, "paper_grid": paper_grid,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clock,
             "accuracy": {"max_rel_err_vs_oracle": float(rel.max()),
                          "per_radius": [float(x) for x in rel],
