@@ -82,9 +82,12 @@ __device__ __forceinline__ float nfw_P(float y)
     return p;
 }
 
-__device__ __forceinline__ float nfw_I_log(float y)
+// y = r^2 rs is passed together with u = 1 + y formed as one fused
+// multiply-add from r^2 and rs (every FP32 product that feeds a sum is written
+// as an explicit fused multiply-add, here and in the packed path, so that no
+// compiler contraction decides the rounding).
+__device__ __forceinline__ float nfw_I_log(float y, float u)
 {
-    const float u = 1.0f + y;
     return fmaf(lg2_approx(u), 0.693147180559945309f, y * rcp_approx(-u));
 }
 
@@ -106,6 +109,10 @@ __device__ __forceinline__ double nfw_I(double y)
 
 // Steps between two tests of the early exit (a power of two).
 constexpr int kExitEvery = 4;
+
+// Added to r^2 in FP32 so that a trajectory through r = 0 exactly gets a
+// finite reciprocal square root.
+constexpr float kR2Guard = 1e-20f;
 
 // A trajectory is finished when its velocity can no longer change: it lies
 // beyond R, where the gradient is exactly zero (mass compensation, App. A),
@@ -158,31 +165,39 @@ struct Tally {
 //   beyond R:              m = 0
 //   NFW, y < 1:            m = P(y) (rs T) - 1/R^3
 //                          (I rinv^3 / I(c) = y^2 P rinv^3 / I(c) = P S^2 rinv / I(c))
-//   NFW, y >= 1, or shell: m = sel rinv^3 - 1/R^3,  sel = I(y)/I(c) or 1
+//   NFW, y >= 1:           m = (I(y)/I(c)) rinv^3 - 1/R^3
+//   shell:                 m = rinv^2 rinv - 1/R^3 (one rounding)
 // The table guarantees Q <= R^2, so r^2 < Q implies r^2 < R^2.
+// The r -> 0 guard is folded into r^2 itself: r^2 = x^2 + (y^2 + 1e-20) with
+// two fused multiply-adds, which changes the bits of r^2 only below ~2e-13 kpc^2.
+__device__ __forceinline__ float guarded_r2(float x, float y)
+{
+    return fmaf(x, x, fmaf(y, y, kR2Guard));
+}
+
 template <class Ctr = NoTally>
 __device__ __forceinline__ float accel_m(float x, float y, float S, float Q, float T,
                                          const HaloF32& hc, Ctr& ctr)
 {
-    const float r2 = fmaf(x, x, y * y);
+    const float r2 = guarded_r2(x, y);
     float m = 0.0f;
     if (r2 < hc.R2) {
-        const float rinv = rsqrt_approx(r2 + 1e-20f);   // r -> 0 guard (changes r^2 < 2e-13 only)
+        const float rinv = rsqrt_approx(r2);
         const float rs = rinv * S;
         const float ys = r2 * rs;
         if (r2 < Q && ys < 1.0f) {
             ctr.add(2);
             m = fmaf(nfw_P(ys), rs * T, -hc.invR3);
         } else {
-            const float rinv3 = (rinv * rinv) * rinv;
-            float sel = 1.0f;
+            const float rinv2 = rinv * rinv;
             if (r2 < Q) {
                 ctr.add(3);
-                sel = nfw_I_log(ys) * hc.invIc;
+                const float sel = nfw_I_log(ys, fmaf(r2, rs, 1.0f)) * hc.invIc;
+                m = fmaf(sel, rinv2 * rinv, -hc.invR3);
             } else {
                 ctr.add(1);
+                m = fmaf(rinv2, rinv, -hc.invR3);
             }
-            m = fmaf(sel, rinv3, -hc.invR3);
         }
     } else {
         ctr.add(0);
@@ -309,7 +324,7 @@ __device__ __forceinline__ void rk4_step(T& x, T& y, T& vx, T& vy, const T* c,
     const T nx = fmaT(c[C_W2], VX4, fmaT(c[C_W1], VX2 + VX3, fmaT(c[C_W0], vx, x)));
     const T ny = fmaT(c[C_W2], VY4, fmaT(c[C_W1], VY2 + VY3, fmaT(c[C_W0], vy, y)));
     // v' = v + (h/6) (BF_a m1 x + 2 BF_m m2 X2 + 2 BF_m m3 X3 + BF_b m4 X4)
-    const T p2x2 = p2 + p2;
+    const T p2x2 = p2 * T(2);   // exact doubling
     const T third = T(1) / T(3);
     const T tx = fmaT(p3, X3, fmaT(p2x2, X2, p1 * x));
     const T ty = fmaT(p3, Y3, fmaT(p2x2, Y2, p1 * y));
@@ -394,41 +409,103 @@ __device__ __forceinline__ f2 nfw_P_x2(f2 y)
 }
 
 // I(y) on the logarithm branch for both lanes (see nfw_I_log).
-__device__ __forceinline__ f2 nfw_I_log_x2(f2 y)
+__device__ __forceinline__ f2 nfw_I_log_x2(f2 y, f2 u)
 {
-    const f2 u = add2(dup(1.0f), y);
     const float ua = f2lo(u), ub = f2hi(u);
     const f2 lg = pk(lg2_approx(ua), lg2_approx(ub));
     const f2 rn = pk(rcp_approx(-ua), rcp_approx(-ub));
     return fma2(lg, dup(0.693147180559945309f), mul2(y, rn));
 }
 
-// m = Mhat/r^3 for both lanes: lane by lane the values of accel_m (FP32).
-// Warp-uniform paths: every lane on the polynomial branch of the NFW part
-// (the common case), every lane on its logarithm branch, or any mix (each
-// branch evaluated for both lanes and selected per lane).  All lanes of the
-// warp execute this function together (the integration loop is warp-uniform).
-__device__ __forceinline__ f2 accel_m_x2(f2 x, f2 y, f2 S, f2 Q, f2 T, const HaloX2& hc)
+// Geometry of one force evaluation for both lanes of a register pair:
+// guarded r^2, 1/r, rs = S/r and y = r^2 rs, and the lane classes (inside the
+// NFW edge; on the polynomial branch of I(y)).
+struct Geo2 {
+    f2 r2, rinv, rs, ys;
+    bool n0, n1, p0, p1;
+};
+
+__device__ __forceinline__ Geo2 geometry_x2(f2 x, f2 y, f2 S, f2 Q)
 {
-    const f2 r2 = fma2(x, x, mul2(y, y));
-    const float r2a = f2lo(r2), r2b = f2hi(r2);
-    const f2 r2g = add2(r2, dup(1e-20f));
-    const f2 rinv = pk(rsqrt_approx(f2lo(r2g)), rsqrt_approx(f2hi(r2g)));
-    const f2 rs = mul2(rinv, S);
-    const f2 ys = mul2(r2, rs);
-    const float ya = f2lo(ys), yb = f2hi(ys);
-    const bool na = r2a < f2lo(Q), nb = r2b < f2hi(Q);          // inside the NFW edge
-    const bool pa = na && ya < 1.0f, pb = nb && yb < 1.0f;     // polynomial branch
-    if (__all_sync(0xffffffffu, pa && pb))
-        return fma2(nfw_P_x2(ys), mul2(rs, T), hc.neg_invR3);
-    const f2 rinv3 = mul2(mul2(rinv, rinv), rinv);
-    if (__all_sync(0xffffffffu, na && nb && !pa && !pb))
-        return fma2(mul2(nfw_I_log_x2(ys), hc.invIc), rinv3, hc.neg_invR3);
-    const f2 mp = fma2(nfw_P_x2(ys), mul2(rs, T), hc.neg_invR3);
-    const f2 Iq = mul2(nfw_I_log_x2(ys), hc.invIc);
-    const f2 ml = fma2(pk(na ? f2lo(Iq) : 1.0f, nb ? f2hi(Iq) : 1.0f), rinv3, hc.neg_invR3);
-    return pk(pa ? f2lo(mp) : (r2a < hc.R2 ? f2lo(ml) : 0.0f),
-              pb ? f2hi(mp) : (r2b < hc.R2 ? f2hi(ml) : 0.0f));
+    Geo2 g;
+    g.r2 = fma2(x, x, fma2(y, y, dup(kR2Guard)));
+    g.rinv = pk(rsqrt_approx(f2lo(g.r2)), rsqrt_approx(f2hi(g.r2)));
+    g.rs = mul2(g.rinv, S);
+    g.ys = mul2(g.r2, g.rs);
+    g.n0 = f2lo(g.r2) < f2lo(Q);
+    g.n1 = f2hi(g.r2) < f2hi(Q);
+    g.p0 = g.n0 && f2lo(g.ys) < 1.0f;
+    g.p1 = g.n1 && f2hi(g.ys) < 1.0f;
+    return g;
+}
+
+// Per-branch formulas of accel_m for both lanes (FP32, the same operations).
+__device__ __forceinline__ f2 m_poly_x2(const Geo2& g, f2 T, const HaloX2& hc)
+{
+    return fma2(nfw_P_x2(g.ys), mul2(g.rs, T), hc.neg_invR3);
+}
+__device__ __forceinline__ f2 m_log_x2(const Geo2& g, f2 rinv2, const HaloX2& hc)
+{
+    const f2 sel = mul2(nfw_I_log_x2(g.ys, fma2(g.r2, g.rs, dup(1.0f))), hc.invIc);
+    return fma2(sel, mul2(rinv2, g.rinv), hc.neg_invR3);
+}
+__device__ __forceinline__ f2 m_shell_x2(const Geo2& g, f2 rinv2, const HaloX2& hc)
+{
+    return fma2(rinv2, g.rinv, hc.neg_invR3);
+}
+// shell or beyond R (0), for lanes outside the NFW edge
+__device__ __forceinline__ f2 m_out_x2(const Geo2& g, const HaloX2& hc)
+{
+    const f2 ms = m_shell_x2(g, mul2(g.rinv, g.rinv), hc);
+    return pk(f2lo(g.r2) < hc.R2 ? f2lo(ms) : 0.0f, f2hi(g.r2) < hc.R2 ? f2hi(ms) : 0.0f);
+}
+// any mix of branches: each formula for both lanes, selected per lane
+__device__ __forceinline__ f2 m_mixed_x2(const Geo2& g, f2 T, const HaloX2& hc)
+{
+    const f2 rinv2 = mul2(g.rinv, g.rinv);
+    const f2 mp = m_poly_x2(g, T, hc);
+    const f2 ml = m_log_x2(g, rinv2, hc);
+    const f2 ms = m_shell_x2(g, rinv2, hc);
+    return pk(g.p0 ? f2lo(mp) : g.n0 ? f2lo(ml) : (f2lo(g.r2) < hc.R2 ? f2lo(ms) : 0.0f),
+              g.p1 ? f2hi(mp) : g.n1 ? f2hi(ml) : (f2hi(g.r2) < hc.R2 ? f2hi(ms) : 0.0f));
+}
+
+// m = Mhat/r^3 at two independent points (a, b) of both lanes: lane by lane
+// the values of accel_m (FP32).  Within one RK4 step the first two stages'
+// positions depend only on the step's start state, and so do the last two
+// given the first two, so their force evaluations are independent and run
+// interleaved.  One warp vote covers all four lane-evaluations (the two
+// points of a pair almost always share their branch): every one on the
+// polynomial branch of the NFW part (the common case), every one on its
+// logarithm branch, every one outside the NFW edge (shell or beyond R), or
+// any mix (each formula evaluated and selected per lane).  All lanes of the
+// warp execute this function together (the integration loop is warp-uniform).
+__device__ __forceinline__ void accel_m_pair_x2(f2 xa, f2 ya, f2 Sa, f2 Qa, f2 Ta,
+                                                f2 xb, f2 yb, f2 Sb, f2 Qb, f2 Tb,
+                                                const HaloX2& hc, f2& ma, f2& mb)
+{
+    const Geo2 ga = geometry_x2(xa, ya, Sa, Qa);
+    const Geo2 gb = geometry_x2(xb, yb, Sb, Qb);
+    const unsigned full = 0xffffffffu;
+    if (__all_sync(full, ga.p0 && ga.p1 && gb.p0 && gb.p1)) {
+        ma = m_poly_x2(ga, Ta, hc);
+        mb = m_poly_x2(gb, Tb, hc);
+        return;
+    }
+    const bool nall = ga.n0 && ga.n1 && gb.n0 && gb.n1;
+    const bool pany = ga.p0 || ga.p1 || gb.p0 || gb.p1;
+    if (__all_sync(full, nall && !pany)) {
+        ma = m_log_x2(ga, mul2(ga.rinv, ga.rinv), hc);
+        mb = m_log_x2(gb, mul2(gb.rinv, gb.rinv), hc);
+        return;
+    }
+    if (__all_sync(full, !(ga.n0 || ga.n1 || gb.n0 || gb.n1))) {
+        ma = m_out_x2(ga, hc);
+        mb = m_out_x2(gb, hc);
+        return;
+    }
+    ma = m_mixed_x2(ga, Ta, hc);
+    mb = m_mixed_x2(gb, Tb, hc);
 }
 
 // One 16-byte entry of the duplicated table (two slots, each a {c, c} pair).
@@ -443,44 +520,42 @@ __device__ __forceinline__ ulonglong2 coef_pair(const uint4* src4, int q)
 // rk4_step for two trajectories at once.  src4 points at the step's 10 x 16
 // bytes of the duplicated table (slot j -> floats 2j, 2j+1); each entry is
 // loaded where it is first needed, which keeps the table out of registers.
+// The four force evaluations run as two independent pairs (stages 1 and 2,
+// then 3 and 4); every value is formed by the same operations as in rk4_step.
 template <bool GTAB>
 __device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const uint4* src4,
                                             const HaloX2& hc)
 {
-    const ulonglong2 q5 = coef_pair<GTAB>(src4, 5), q6 = coef_pair<GTAB>(src4, 6);
-    const ulonglong2 q8 = coef_pair<GTAB>(src4, 8);
-    const f2 S0{q5.x}, S1{q5.y}, S2{q6.x}, Q0{q6.y}, T0{q8.x}, T1{q8.y};
-    const f2 m1 = accel_m_x2(x, y, S0, Q0, T0, hc);
-    const ulonglong2 q0 = coef_pair<GTAB>(src4, 0), q1 = coef_pair<GTAB>(src4, 1);
-    const f2 MA1{q0.x}, MA2{q0.y}, MA3{q1.x}, B1{q1.y};
-    const f2 p1 = mul2(B1, m1);
+    const ulonglong2 q0 = coef_pair<GTAB>(src4, 0);
+    const f2 MA1{q0.x}, MA2{q0.y};
     const f2 X2 = fma2(MA1, vx, x), Y2 = fma2(MA1, vy, y);
+    const ulonglong2 q5 = coef_pair<GTAB>(src4, 5), q6 = coef_pair<GTAB>(src4, 6);
+    const ulonglong2 q7 = coef_pair<GTAB>(src4, 7), q8 = coef_pair<GTAB>(src4, 8);
+    const f2 S0{q5.x}, S1{q5.y}, Q0{q6.y}, Q1{q7.x}, T0{q8.x}, T1{q8.y};
+    f2 m1, m2;
+    accel_m_pair_x2(x, y, S0, Q0, T0, X2, Y2, S1, Q1, T1, hc, m1, m2);
+    const ulonglong2 q1 = coef_pair<GTAB>(src4, 1), q2 = coef_pair<GTAB>(src4, 2);
+    const f2 MA3{q1.x}, B1{q1.y}, B2{q2.x};
+    const f2 p1 = mul2(B1, m1);
     const f2 VX2 = fma2(p1, x, vx), VY2 = fma2(p1, y, vy);
-
-    const ulonglong2 q7 = coef_pair<GTAB>(src4, 7);
-    const f2 Q1{q7.x}, Q2{q7.y};
-    const f2 m2 = accel_m_x2(X2, Y2, S1, Q1, T1, hc);
-    const ulonglong2 q2 = coef_pair<GTAB>(src4, 2);
-    const f2 B2{q2.x}, B3{q2.y};
     const f2 p2 = mul2(B2, m2);
-    const f2 X3 = fma2(MA2, VX2, x), Y3 = fma2(MA2, VY2, y);
     const f2 VX3 = fma2(p2, X2, vx), VY3 = fma2(p2, Y2, vy);
-
-    const f2 m3 = accel_m_x2(X3, Y3, S1, Q1, T1, hc);
-    const f2 p3 = mul2(B3, m3);
+    const f2 X3 = fma2(MA2, VX2, x), Y3 = fma2(MA2, VY2, y);
     const f2 X4 = fma2(MA3, VX3, x), Y4 = fma2(MA3, VY3, y);
-    const f2 VX4 = fma2(p3, X3, vx), VY4 = fma2(p3, Y3, vy);
 
     const ulonglong2 q9 = coef_pair<GTAB>(src4, 9);
-    const f2 T2{q9.x};
-    const f2 m4 = accel_m_x2(X4, Y4, S2, Q2, T2, hc);
+    const f2 S2{q6.x}, Q2{q7.y}, T2{q9.x};
+    f2 m3, m4;
+    accel_m_pair_x2(X3, Y3, S1, Q1, T1, X4, Y4, S2, Q2, T2, hc, m3, m4);
     const ulonglong2 q3 = coef_pair<GTAB>(src4, 3), q4 = coef_pair<GTAB>(src4, 4);
-    const f2 B4{q3.x}, W0{q3.y}, W1{q4.x}, W2{q4.y};
+    const f2 B3{q2.y}, B4{q3.x}, W0{q3.y}, W1{q4.x}, W2{q4.y};
+    const f2 p3 = mul2(B3, m3);
+    const f2 VX4 = fma2(p3, X3, vx), VY4 = fma2(p3, Y3, vy);
     const f2 p4 = mul2(B4, m4);
 
     const f2 nx = fma2(W2, VX4, fma2(W1, add2(VX2, VX3), fma2(W0, vx, x)));
     const f2 ny = fma2(W2, VY4, fma2(W1, add2(VY2, VY3), fma2(W0, vy, y)));
-    const f2 p2x2 = add2(p2, p2);
+    const f2 p2x2 = mul2(p2, dup(2.0f));   // exact doubling
     const f2 third = dup(1.0f / 3.0f);
     const f2 tx = fma2(p3, X3, fma2(p2x2, X2, mul2(p1, x)));
     const f2 ty = fma2(p3, Y3, fma2(p2x2, Y2, mul2(p1, y)));
@@ -554,7 +629,6 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         T* state = reinterpret_cast<T*>(P.state);
 
         T x[TPT], y[TPT], vx[TPT], vy[TPT];
-        int tj[TPT], tk[TPT];
         bool act[TPT];
         bool done = true;            // every trajectory of this lane is finished
 #pragma unroll
@@ -563,8 +637,6 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             act[i] = t < n_seg;
             done &= !act[i];
             const int tt = act[i] ? t : 0;
-            tj[i] = tt / n_mu;
-            tk[i] = tt - tj[i] * n_mu;
             if (state && s_begin > 0) {          // resume a served request
                 const T* st = state + ((size_t)seg * n_seg + tt) * 4;
                 x[i] = st[0];
@@ -572,11 +644,12 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                 vx[i] = st[2];
                 vy[i] = st[3];
             } else {                             // Sec. II.C initial conditions
-                const T v0 = reinterpret_cast<const T*>(P.v0)[tj[i]];
+                const int j = tt / n_mu, k = tt - (tt / n_mu) * n_mu;
+                const T v0 = reinterpret_cast<const T*>(P.v0)[j];
                 x[i] = x0;
                 y[i] = T(0);
-                vx[i] = v0 * reinterpret_cast<const T*>(P.mu)[tk[i]];
-                vy[i] = v0 * reinterpret_cast<const T*>(P.smu)[tk[i]];
+                vx[i] = v0 * reinterpret_cast<const T*>(P.mu)[k];
+                vy[i] = v0 * reinterpret_cast<const T*>(P.smu)[k];
             }
         }
 
@@ -666,6 +739,15 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                 const int t = tis * P.tile + i * blockDim.x + threadIdx.x;
                 reinterpret_cast<T*>(P.qi)[(size_t)seg * n_seg + t] = qf[i];
             }
+        }
+        // momentum and direction nodes of each trajectory (recomputed here
+        // rather than kept live through the step loop)
+        int tj[TPT], tk[TPT];
+#pragma unroll
+        for (int i = 0; i < TPT; ++i) {
+            const int t = act[i] ? tis * P.tile + i * blockDim.x + threadIdx.x : 0;
+            tj[i] = t / n_mu;
+            tk[i] = t - tj[i] * n_mu;
         }
         const int nm = P.n_mass;
         double* part = P.partials + ((size_t)seg * tps + tis) * 2 * nm;
