@@ -41,13 +41,15 @@
  * Units (a choice; the paper gives none): comoving length kpc, velocity km/s,
  * mass Msun, H in km/s/kpc, momentum q in units of k_B T0.
  *
- * Pins (tests/test_oracle_pins.py) tie every function here to something other
- * than itself: printed values, closed forms, invariants, library routines,
- * independent formulations.  Parity unpinned: the absolute n/nbar that
- * or_profile and or_profile_masses return at radii inside a halo.  The paper
- * prints no such values and its figures carry no recoverable data; only the
- * parts of the computation and the limits (no halo, far from the halo,
- * clustering inside, ordering in mass) are pinned.
+ * Pins (tests/test_oracle_pins.py, tests/test_oracle_quadrature.py) tie every
+ * function here to something other than itself: printed values, closed forms,
+ * invariants, library routines, independent formulations.  The quadrature
+ * assembly of or_profile and or_profile_masses (the q^3 measure in ln q, the
+ * direction weights, the background, the mass scaling) is pinned against
+ * adaptive quadrature in linear P at a well-conditioned radius with strong
+ * clustering.  Parity unpinned: the absolute n/nbar at radii in halo cores,
+ * where the fixed-step map is chaotic; the paper prints no such values and its
+ * figures carry no recoverable data.
  */
 #include <math.h>
 #include <stdlib.h>
