@@ -181,6 +181,8 @@ typedef struct nu_opts {
     nu_free_fn free;
     void* alloc_ctx;
     void* stream;        /* cudaStream_t used for uploads during create           */
+    double timeout_ms;   /* bound on the host's wait in synchronous calls
+                            (nu_profile_compute_noalloc); 0 -> 60000 ms      */
 } nu_opts;
 
 #define NU_MAX_STEPS 3000  /* the per-step coefficient table (80 B per step in FP32,
@@ -414,26 +416,34 @@ NU_API void nu_server_destroy(nu_server* s);
  * call, with every device buffer the trajectory kernel needs (descriptor,
  * coefficient table, nodes and weights, tile sums, counters) placed in one
  * file-scope __device__ array of NU_NOALLOC_MAX_BYTES that every GPU loading
- * the library keeps until the process exits, and the host tables built in a
- * static host buffer.  It calls no cudaMalloc, cudaFree or other allocating
- * routine.
+ * the library keeps until the process exits, and the host tables built (by
+ * the same routines as nu_profile_create) in a static host buffer of the same
+ * size.  It calls no cudaMalloc, cudaFree or other allocating routine.  The
+ * results are bitwise those of nu_profile_create/run/result at the same
+ * launch shape.
  *   Inputs are the same as nu_profile_create (opts may be NULL; opts->flags
- *   must be 0 and the allocator hooks are ignored); n_over_nbar and err_est
- *   (may be NULL) are host arrays of n_radii doubles.  The work runs on
- *   `stream` and the call returns after it has finished.
- *   Set-up: the first call on each device looks up the array's device
- *   address (cudaGetSymbolAddress) with that device current; make that first
- *   call before any stream capture.
+ *   must be 0 and the allocator hooks are ignored; opts->timeout_ms bounds
+ *   the wait); n_over_nbar and err_est (may be NULL) are host arrays of
+ *   n_radii doubles.  The work runs on `stream`, which must not be capturing,
+ *   and the call returns after it has finished.
+ *   Set-up: every call looks up the array's device address
+ *   (cudaGetSymbolAddress) with the current device; the first call on a
+ *   device also loads the module there, so make it before any stream capture
+ *   (other threads' captures must use the relaxed or thread-local mode).
  *   Sharing: all calls use the same array.  A process-wide lock serializes
  *   the calls and each waits for its own work, so calls from this library
- *   never overlap; any other work that touched the array while a call ran
- *   would race with it.  The array keeps the last call's contents; each call
- *   clears the counters that must start at zero.
+ *   never overlap on the GPU; any other work that touched the array while a
+ *   call ran would race with it.  The array keeps the last call's contents;
+ *   each call clears the counters that must start at zero.
+ *   Timeout: if the call's work has not finished within timeout_ms the call
+ *   returns NU_ETIMEDOUT and its work keeps the array; later calls on that
+ *   device first wait (again bounded) for that work, so keep its stream alive
+ *   until a later call has returned something other than NU_ETIMEDOUT.
  *   Errors: NU_EINVAL, NU_ENOTSUP (the packed shape tpt = 3, a mass-reuse
  *   relic or a tabulated f: this entry point computes one closed-form
- *   distribution for one mass), NU_ETOOBIG (the request needs
- *   more than NU_NOALLOC_MAX_BYTES, e.g. too many radii x tiles or steps),
- *   NU_EDEVICE, NU_ECUDA. */
+ *   distribution for one mass), NU_ETOOBIG (the request's device buffers, or
+ *   its host tables, need more than NU_NOALLOC_MAX_BYTES, e.g. too many
+ *   radii x tiles or steps), NU_ETIMEDOUT, NU_EDEVICE, NU_ECUDA. */
 NU_API int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* halo,
                                       const nu_relic* relic, const double* radii, int n_radii,
                                       const nu_pgrid* p_grid, const nu_opts* opts,

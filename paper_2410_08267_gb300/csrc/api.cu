@@ -381,7 +381,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     const size_t o_wmu = carve((size_t)nmu * sizeof(double));
     const size_t o_mass = carve((size_t)nm * 3 * sizeof(double));   // scales, then norms
     const int nft = relic->f_kind == NU_F_TABLE ? relic->n_table : 0;
-    const size_t o_ftab = carve((size_t)(nft > 0 ? nft : 1) * sz);   // tabulated f
+    const size_t o_ftab = carve((size_t)(nft > 0 ? nft : 1) * sizeof(double));   // tabulated f (FP64)
     const size_t upload_end = off;                         // everything above is uploaded
     // tile sums sized for the smallest tile shape, so that any batch shape fits
     const size_t tps_alloc = (size_t)(((long long)nq * nmu + kMinTile - 1) / kMinTile);
@@ -465,8 +465,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     put<double>(stage, o_mass, mass_s.data(), nm);
     put<double>(stage, o_mass + nm * sizeof(double), norms.data(), 2 * (size_t)nm);
     if (nft > 0) {
-        if (fp64) put<double>(stage, o_ftab, relic->f_table, nft);
-        else put<float>(stage, o_ftab, relic->f_table, nft);
+        put<double>(stage, o_ftab, relic->f_table, nft);
     }
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);

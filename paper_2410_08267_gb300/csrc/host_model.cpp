@@ -153,10 +153,9 @@ double relic_f(const nu_relic& relic, double q)
 // One RK4 step of size -h needs the stage redshifts at u = -n h, -(n+1/2) h and
 // -(n+1) h; each is computed from the integer step index (1+z = e^{k h/2}),
 // so no time variable is ever accumulated.
-void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps,
-                std::vector<double>& tab)
+void coef_table_into(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps,
+                     double* tab)
 {
-    tab.assign((size_t)n_steps * C_COUNT, 0.0);
     const double h = std::log1p(d.z_end) / n_steps;
     auto stage = [&](long k, double& A, double& BF, double& S, double& Q) {
         const double zp1 = std::exp(0.5 * h * (double)k);
@@ -179,7 +178,7 @@ void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, in
         double Am, BFm, Sm, Qm, Ab, BFb, Sb, Qb;
         stage(2L * n + 1, Am, BFm, Sm, Qm);
         stage(2L * n + 2, Ab, BFb, Sb, Qb);
-        double* t = &tab[(size_t)n * C_COUNT];
+        double* t = tab + (size_t)n * C_COUNT;
         t[C_MA1] = -0.5 * h * Aa;
         t[C_MA2] = -0.5 * h * Am;
         t[C_MA3] = -h * Am;
@@ -207,24 +206,28 @@ void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, in
     }
 }
 
+void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps,
+                std::vector<double>& tab)
+{
+    tab.assign((size_t)n_steps * C_COUNT, 0.0);
+    coef_table_into(cosmo, halo, d, n_steps, tab.data());
+}
+
 // |P| nodes: log-spaced on [q_min, q_max]; the integral of P^2 f dP is taken
 // as the trapezoid rule in ln q of q^3 f, so the weight folded with q^3 is
 // returned.  The coarse weights integrate the same range on every other node
 // (with one fine interval at the top when n is even) and feed the error estimate.
-void log_nodes(int n, double q_min, double q_max, std::vector<double>& q,
-               std::vector<double>& wl, std::vector<double>& wlc)
+void log_nodes_into(int n, double q_min, double q_max, double* q, double* wl, double* wlc)
 {
-    q.resize(n);
-    wl.assign(n, 0.0);
-    wlc.assign(n, 0.0);
     const double lmin = std::log(q_min);
     const double dl = (std::log(q_max) - lmin) / (n - 1);
     for (int j = 0; j < n; ++j) {
         q[j] = std::exp(lmin + dl * j);
         wl[j] = (j == 0 || j == n - 1) ? 0.5 * dl : dl;
+        wlc[j] = 0.0;
     }
     if (n < 3) {
-        wlc = wl;
+        for (int j = 0; j < n; ++j) wlc[j] = wl[j];
     } else {
         const int top = (n % 2 == 1) ? n - 1 : n - 2;   // last even node of the coarse rule
         for (int j = 0; j <= top; j += 2)
@@ -241,10 +244,14 @@ void log_nodes(int n, double q_min, double q_max, std::vector<double>& q,
     }
 }
 
-// Gauss-Legendre rule on [-1, 1]: roots of P_n from Tricomi's asymptotic
-// estimate refined by Newton steps, with P_n and P_n' from the three-term
-// recurrence; weights 2 / ((1 - x^2) P_n'(x)^2).  Nodes ascend.
-static void gauss_legendre_compute(int n, std::vector<double>& x, std::vector<double>& w);
+void log_nodes(int n, double q_min, double q_max, std::vector<double>& q,
+               std::vector<double>& wl, std::vector<double>& wlc)
+{
+    q.assign(n, 0.0);
+    wl.assign(n, 0.0);
+    wlc.assign(n, 0.0);
+    log_nodes_into(n, q_min, q_max, q.data(), wl.data(), wlc.data());
+}
 
 // Rules are cached per n (requests of a scan share a few direction grids).
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w)
@@ -260,15 +267,19 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w)
             return;
         }
     }
-    gauss_legendre_compute(n, x, w);
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    gauss_legendre_into(n, x.data(), w.data());
     std::lock_guard<std::mutex> g(mu);
     if (cache.size() < 4096) cache[n] = {x, w};
 }
 
-static void gauss_legendre_compute(int n, std::vector<double>& x, std::vector<double>& w)
+// Gauss-Legendre rule on [-1, 1]: roots of P_n from Tricomi's asymptotic
+// estimate refined by Newton steps, with P_n and P_n' from the three-term
+// recurrence; weights 2 / ((1 - x^2) P_n'(x)^2).  Nodes ascend.
+void gauss_legendre_into(int n, double* x, double* w)
 {
-    x.assign(n, 0.0);
-    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) x[i] = w[i] = 0.0;
     const int half = (n + 1) / 2;
     for (int i = 0; i < half; ++i) {
         const double th = kPi * (4.0 * (i + 1) - 1.0) / (4.0 * n + 2.0);
@@ -324,7 +335,7 @@ long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_m
     b += 2 * align256((size_t)n_q * sizeof(double));             // wq, wqc
     b += align256((size_t)n_mu * sizeof(double));                // wmu
     b += align256((size_t)n_mass * 3 * sizeof(double));          // mass scales, normalisations
-    b += align256((size_t)(n_ftab > 0 ? n_ftab : 1) * sz);       // tabulated f
+    b += align256((size_t)(n_ftab > 0 ? n_ftab : 1) * sizeof(double));   // tabulated f (FP64)
     if (h2d_bytes) *h2d_bytes = (long long)b;                    // everything above is uploaded
     b += align256((size_t)n_radii * tiles_per_seg * 2 * n_mass * sizeof(double));
     b += align256((size_t)n_radii * sizeof(unsigned));

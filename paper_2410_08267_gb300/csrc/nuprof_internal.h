@@ -63,10 +63,15 @@ double hubble(const nu_cosmo& cosmo, const Derived& d, double z);
 double growth_xi(const nu_halo& halo, const Derived& d, double z);
 double coupling_kappa(const nu_halo& halo, double z);
 double relic_f(const nu_relic& relic, double q);
+// Host tables, written into caller memory (no allocation) or into vectors.
+void coef_table_into(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps,
+                     double* table);   // [n_steps][C_COUNT]
 void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps,
                 std::vector<double>& table);
+void log_nodes_into(int n, double q_min, double q_max, double* q, double* wl, double* wl_coarse);
 void log_nodes(int n, double q_min, double q_max, std::vector<double>& q,
                std::vector<double>& wl, std::vector<double>& wl_coarse);
+void gauss_legendre_into(int n, double* x, double* w);   // computed, not cached
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 void resolve_opts(const nu_opts* in, nu_opts& out);
 long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_mu,
@@ -98,7 +103,7 @@ struct DevProblem {
     double f_p0;
     int f_kind;
     int n_ftab;             // NU_F_TABLE: nodes of ftab
-    const void* ftab;       // NU_F_TABLE: [n_ftab] f values in the state precision
+    const void* ftab;       // NU_F_TABLE: [n_ftab] f values (FP64)
     double ftab_q0;         // first node (k_B T0)
     double ftab_q1;         // last node
     double ftab_scale;      // (n_ftab - 1) / ln(q_last / q_first)

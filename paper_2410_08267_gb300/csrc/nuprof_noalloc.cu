@@ -9,14 +9,15 @@
 // request descriptor, the per-step coefficient table, the quadrature nodes and
 // weights, the per-tile partial sums, the per-radius completion counters and
 // the work counter) lives in one file-scope __device__ array of fixed size.
-// Host-side tables are built in a static host buffer of the same size, so the
-// call performs no heap allocation either.
+// The host tables are built by the same routines as nu_profile_create, written
+// into a static host buffer, so the call performs no heap allocation either.
 #include <cuda_runtime.h>
 
-#include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <thread>
 
 #include "nuprof_internal.h"
 
@@ -25,151 +26,48 @@ namespace {
 
 constexpr size_t kArenaBytes = NU_NOALLOC_MAX_BYTES;
 constexpr int kMaxDevices = 64;
+constexpr double kDefaultTimeoutMs = 60000.0;
 
 // Device scratch shared by every call on a GPU; every GPU that loads the
 // library holds it until the process exits.  In host code this name is only a
 // host-side stand-in: the device address comes from cudaGetSymbolAddress.
 __device__ __align__(256) unsigned char g_arena[kArenaBytes];
 
-// Host staging of the uploaded part of the arena (static: no heap allocation).
+// Host side of a call: the staged upload image of the arena at the front,
+// then the FP64 tables and the read-back results (static: no heap allocation).
 alignas(256) unsigned char g_stage[kArenaBytes];
 std::mutex g_lock;
-void* g_arena_dev[kMaxDevices];      // device address of g_arena, per device
+
+// Per device: a call whose wait ran out left its work on `stream`; the array
+// is not touched again until that stream has drained.
+struct Pending {
+    bool active = false;
+    cudaStream_t stream = nullptr;
+};
+Pending g_pending[kMaxDevices];
 
 size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Device address of the arena on the current device (looked up once per device).
-int arena_address(void** out)
+// Wait until every operation enqueued on `s` so far has finished, for at most
+// timeout_ms: NU_OK, NU_ETIMEDOUT, or NU_ECUDA if the stream reports an error.
+int wait_bounded(cudaStream_t s, double timeout_ms)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return NU_ECUDA;
-    }
-    if (dev < 0 || dev >= kMaxDevices) return NU_ENOTSUP;
-    if (!g_arena_dev[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_arena) != cudaSuccess || !p) {
+    using clock = std::chrono::steady_clock;
+    const auto t0 = clock::now();
+    for (int it = 0;; ++it) {
+        const cudaError_t e = cudaStreamQuery(s);
+        if (e == cudaSuccess) return NU_OK;
+        if (e != cudaErrorNotReady) {
             cudaGetLastError();
             return NU_ECUDA;
         }
-        g_arena_dev[dev] = p;
+        const double ms = std::chrono::duration<double, std::milli>(clock::now() - t0).count();
+        if (ms >= timeout_ms) return NU_ETIMEDOUT;
+        if (it < 2000)
+            std::this_thread::yield();
+        else
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    *out = g_arena_dev[dev];
-    return NU_OK;
-}
-
-// The per-step coefficient table, written into caller memory (the same
-// stage definitions as the table of nu_profile_create: Eq. eoms in ln a with
-// the App. A gradient at u = -n h, -(n+1/2) h, -(n+1) h).
-void coef_table_into(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps,
-                     double* tab)
-{
-    const double h = std::log1p(d.z_end) / n_steps;
-    for (int n = 0; n < n_steps; ++n) {
-        double A[3], BF[3], S[3], Q[3];
-        for (int s = 0; s < 3; ++s) {
-            const double k = 2.0 * n + s;
-            const double zp1 = std::exp(0.5 * h * k);
-            const double z = std::expm1(0.5 * h * k);
-            const double H = hubble(cosmo, d, z);
-            A[s] = zp1 * zp1 / H;
-            BF[s] = kG * coupling_kappa(halo, z) * zp1 * growth_xi(halo, d, z) * halo.M_h / H;
-            S[s] = d.r_s > 0.0 ? 1.0 / (zp1 * d.r_s) : 0.0;
-            const double rin = std::min(d.r200 * zp1, d.R);   // edge never beyond R
-            Q[s] = rin * rin;
-        }
-        double* t = tab + (size_t)n * C_COUNT;
-        t[C_MA1] = -0.5 * h * A[0];
-        t[C_MA2] = -0.5 * h * A[1];
-        t[C_MA3] = -h * A[1];
-        t[C_B1] = 0.5 * h * BF[0];
-        t[C_B2] = 0.5 * h * BF[1];
-        t[C_B3] = h * BF[1];
-        t[C_B4] = h / 6.0 * BF[2];
-        t[C_W0] = -h / 6.0 * A[0];
-        t[C_W1] = -h / 3.0 * A[1];
-        t[C_W2] = -h / 6.0 * A[2];
-        t[C_S0] = S[0];
-        t[C_S1] = S[1];
-        t[C_S2] = S[2];
-        t[C_Q0] = Q[0];
-        t[C_Q1] = Q[1];
-        t[C_Q2] = Q[2];
-        t[C_T0] = S[0] / d.Ic;
-        t[C_T1] = S[1] / d.Ic;
-        t[C_T2] = S[2] / d.Ic;
-        t[C_PAD] = 0.0;
-    }
-}
-
-// Log-spaced q nodes with trapezoid-in-ln q weights times q^3 (fine and
-// every-other-node rules), as in nu_profile_create.
-void log_nodes_into(int n, double q_min, double q_max, double* q, double* wl, double* wlc)
-{
-    const double lmin = std::log(q_min);
-    const double dl = (std::log(q_max) - lmin) / (n - 1);
-    for (int j = 0; j < n; ++j) {
-        q[j] = std::exp(lmin + dl * j);
-        wl[j] = (j == 0 || j == n - 1) ? 0.5 * dl : dl;
-        wlc[j] = 0.0;
-    }
-    if (n < 3) {
-        for (int j = 0; j < n; ++j) wlc[j] = wl[j];
-    } else {
-        const int top = (n % 2 == 1) ? n - 1 : n - 2;
-        for (int j = 0; j <= top; j += 2) wlc[j] = (j == 0 || j == top) ? dl : 2.0 * dl;
-        if (top == n - 2) {
-            wlc[n - 2] += 0.5 * dl;
-            wlc[n - 1] += 0.5 * dl;
-        }
-    }
-    for (int j = 0; j < n; ++j) {
-        const double q3 = q[j] * q[j] * q[j];
-        wl[j] *= q3;
-        wlc[j] *= q3;
-    }
-}
-
-// Gauss-Legendre nodes (ascending) and weights on [-1, 1]: Newton iteration
-// from Tricomi's estimate, as in nu_profile_create.
-void gauss_legendre_into(int n, double* x, double* w)
-{
-    for (int i = 0; i < n; ++i) x[i] = w[i] = 0.0;
-    const int half = (n + 1) / 2;
-    for (int i = 0; i < half; ++i) {
-        const double th = kPi * (4.0 * (i + 1) - 1.0) / (4.0 * n + 2.0);
-        double r = (1.0 - (n - 1.0) / (8.0 * n * (double)n * n)) * std::cos(th);
-        for (int it = 0; it < 64; ++it) {
-            double p0 = 1.0, p1 = r;
-            for (int k = 2; k <= n; ++k) {
-                const double p2 = ((2.0 * k - 1.0) * r * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = p2;
-            }
-            const double pn = (n == 1) ? r : p1;
-            const double pm = (n == 1) ? 1.0 : p0;
-            const double dp = n * (pm - r * pn) / (1.0 - r * r);
-            const double step = pn / dp;
-            r -= step;
-            if (std::fabs(step) <= 1e-17) break;
-        }
-        double p0 = 1.0, p1 = r;
-        for (int k = 2; k <= n; ++k) {
-            const double p2 = ((2.0 * k - 1.0) * r * p1 - (k - 1.0) * p0) / k;
-            p0 = p1;
-            p1 = p2;
-        }
-        const double pn = (n == 1) ? r : p1;
-        const double pm = (n == 1) ? 1.0 : p0;
-        const double dp = n * (pm - r * pn) / (1.0 - r * r);
-        const double wi = 2.0 / ((1.0 - r * r) * dp * dp);
-        x[n - 1 - i] = r;
-        x[i] = -r;
-        w[n - 1 - i] = wi;
-        w[i] = wi;
-    }
-    if (n % 2 == 1) x[n / 2] = 0.0;
 }
 
 template <typename T>
@@ -192,7 +90,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     if (!n_over_nbar) return NU_EINVAL;
     nu_opts o;
     resolve_opts(opts, o);
-    if (o.flags != 0) return NU_EINVAL;
+    if (o.flags != 0 || o.timeout_ms < 0.0) return NU_EINVAL;
     if (o.tpt == kTptPacked) return NU_ENOTSUP;   // the packed table is not staged here
     if (relic && relic->n_masses > 0) return NU_ENOTSUP;   // one mass per call
     if (relic && relic->f_kind == NU_F_TABLE) return NU_ENOTSUP;   // closed-form f only
@@ -201,6 +99,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     Derived d;
     rc = derive(*cosmo, *halo, o, d);
     if (rc != NU_OK) return rc;
+    const double timeout_ms = o.timeout_ms > 0.0 ? o.timeout_ms : kDefaultTimeoutMs;
 
     const int nq = p_grid->n_q, nmu = p_grid->n_mu, N = o.n_steps;
     const long long seg = (long long)nq * nmu;
@@ -210,7 +109,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     if (n_tiles_ll > (1LL << 30)) return NU_ETOOBIG;
     const int tps = (int)tps_ll, n_tiles = (int)n_tiles_ll;
 
-    // arena layout (the same order as the buffers of nu_profile_create)
+    // Device layout (the same order as the buffers of nu_profile_create).
     const bool fp64 = o.precision == NU_FP64;
     const size_t sz = fp64 ? sizeof(double) : sizeof(float);
     size_t off = 0;
@@ -232,23 +131,43 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     const size_t o_cnt = carve((size_t)n_radii * sizeof(unsigned));
     const size_t o_out = carve((size_t)n_radii * sizeof(double));
     const size_t o_err = carve((size_t)n_radii * sizeof(double));
-    // host scratch for the FP64 tables, placed after the uploaded image
-    const size_t h_coef = carve((size_t)N * C_COUNT * sizeof(double));
-    const size_t h_q = carve((size_t)nq * sizeof(double) * 3);
-    const size_t h_mu = carve((size_t)nmu * sizeof(double) * 3);
-    const size_t h_x0 = carve((size_t)n_radii * sizeof(double));
-    const size_t h_out = carve((size_t)n_radii * 2 * sizeof(double));
-    if (off > kArenaBytes) return NU_ETOOBIG;
+    if (off > kArenaBytes) return NU_ETOOBIG;             // the device array
+    // Host layout of the static staging buffer: the upload image, then the
+    // FP64 tables and the read-back results.
+    size_t hoff = upload_end;
+    auto hcarve = [&](size_t bytes) { size_t at = hoff; hoff += up256(bytes); return at; };
+    const size_t h_coef = hcarve((size_t)N * C_COUNT * sizeof(double));
+    const size_t h_q = hcarve((size_t)nq * sizeof(double) * 3);
+    const size_t h_mu = hcarve((size_t)nmu * sizeof(double) * 3);
+    const size_t h_x0 = hcarve((size_t)n_radii * sizeof(double));
+    const size_t h_out = hcarve((size_t)n_radii * 2 * sizeof(double));
+    if (hoff > kArenaBytes) return NU_ETOOBIG;            // the host buffer
 
     std::lock_guard<std::mutex> guard(g_lock);
+    int dev_id = 0;
+    if (cudaGetDevice(&dev_id) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    if (dev_id < 0 || dev_id >= kMaxDevices) return NU_ENOTSUP;
+    Pending& pend = g_pending[dev_id];
+    if (pend.active) {                                    // a timed-out call's work may still run
+        rc = wait_bounded(pend.stream, timeout_ms);
+        if (rc != NU_OK) return rc;
+        pend.active = false;
+    }
+    // Device address of the array on the current device, looked up on every
+    // call (a context re-created after a reset may place it elsewhere).
     void* arena = nullptr;
-    rc = arena_address(&arena);
-    if (rc != NU_OK) return rc;
+    if (cudaGetSymbolAddress(&arena, g_arena) != cudaSuccess || !arena) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
     unsigned char* dev = static_cast<unsigned char*>(arena);
     unsigned char* st = g_stage;
     std::memset(st, 0, upload_end);
 
-    // ---- FP64 tables in the host scratch part of the static buffer ----
+    // ---- FP64 tables (the routines of nu_profile_create) in the host part ----
     double* coef = reinterpret_cast<double*>(st + h_coef);
     double* q = reinterpret_cast<double*>(st + h_q);
     double* wq = q + nq;
@@ -263,7 +182,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     const double kT0 = kKB * cosmo->T0_K;
     double nb = 0.0, nbc = 0.0;
     for (int j = 0; j < nq; ++j) {
-        const double f = relic_f(*relic, q[j]);
+        const double f = relic_f(*relic, 1.0 * q[j]);
         nb += wq[j] * f;
         nbc += wqc[j] * f;
         q[j] = kC * q[j] * kT0 / relic->m_eV;             // now the start speed v0 (km/s)
@@ -328,12 +247,11 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     const double mass[3] = {1.0, 1.0 / (2.0 * nb), 1.0 / (2.0 * nbc)};
     put_into<double>(st, o_mass, mass, 3);
 
-    int per_sm = 0, sms = 0, devid = 0;
+    int per_sm = 0, sms = 0;
     const size_t smem = coef_smem_bytes(o.precision, N, o.tpt);
     rc = max_ctas_per_sm(o.precision, o.tpt, o.block, smem, &per_sm);
     if (rc != NU_OK) return rc;
-    if (cudaGetDevice(&devid) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devid) != cudaSuccess ||
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         return NU_ECUDA;
@@ -341,31 +259,41 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     const int grid = n_tiles < per_sm * sms ? n_tiles : per_sm * sms;
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // The arena keeps the previous call's contents: the control words (work
+    // The array keeps the previous call's contents: the control words (work
     // counter, status) are part of the zeroed upload and the per-radius
     // completion counters are cleared explicitly.
     if (cudaMemcpyAsync(dev, st, upload_end, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(dev + o_cnt, 0, (size_t)n_radii * sizeof(unsigned), s) != cudaSuccess) {
         cudaGetLastError();
+        // nothing may still read the staging buffer or write the array
+        if (wait_bounded(s, timeout_ms) != NU_OK) pend = {true, s};
         return NU_ECUDA;
     }
     rc = launch_traj(o.precision, o.tpt, o.block, grid, smem,
                      reinterpret_cast<const DevProblem*>(dev + o_prob),
                      reinterpret_cast<const int*>(dev + o_pref), 1, n_tiles,
                      reinterpret_cast<unsigned*>(dev + o_ctrl), stream);
-    if (rc != NU_OK) {
-        cudaGetLastError();
-        return rc;
-    }
+    if (rc != NU_OK) cudaGetLastError();
+    // Wait for this call's own work (bounded) before reading back: a copy
+    // into the (pageable) static buffer would block until the kernel ends.
+    // If the work does not finish in time, later calls wait for it before
+    // they touch the array.
+    int wrc = wait_bounded(s, timeout_ms);
+    if (wrc == NU_ETIMEDOUT) pend = {true, s};
+    if (rc != NU_OK) return rc;
+    if (wrc != NU_OK) return wrc;
     double* host_out = reinterpret_cast<double*>(st + h_out);
     if (cudaMemcpyAsync(host_out, dev + o_out, (size_t)n_radii * sizeof(double),
                         cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(host_out + n_radii, dev + o_err, (size_t)n_radii * sizeof(double),
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess) {
         cudaGetLastError();
+        if (wait_bounded(s, timeout_ms) != NU_OK) pend = {true, s};
         return NU_ECUDA;
     }
+    wrc = wait_bounded(s, timeout_ms);
+    if (wrc == NU_ETIMEDOUT) pend = {true, s};
+    if (wrc != NU_OK) return wrc;
     for (int i = 0; i < n_radii; ++i)
         if (!std::isfinite(host_out[i])) return NU_EDEVICE;
     std::memcpy(n_over_nbar, host_out, (size_t)n_radii * sizeof(double));

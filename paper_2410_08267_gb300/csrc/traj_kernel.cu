@@ -245,38 +245,26 @@ template <> struct PrecTraits<double> {
     }
 };
 
-// Initial distribution f(q) (Sec. II.C, Sec. IV.B) in the state precision.
-// The tabulated kind is linear in ln q between log-spaced nodes, the first
-// value below the first node and 0 above the last.
-__device__ __forceinline__ float log_T(float v) { return logf(v); }
-__device__ __forceinline__ double log_T(double v) { return log(v); }
-
-template <typename T>
-__device__ __forceinline__ T relic_f_table(const DevProblem& P, T q)
+// Initial distribution f(q) (Sec. II.C, Sec. IV.B), evaluated in FP64 in both
+// precision modes (it runs once per trajectory and mass, in the epilogue).
+// The tabulated kind is linear in ln q between log-spaced nodes (stored in
+// FP64), the first value below the first node and 0 above the last.
+__device__ __forceinline__ double relic_f_table(const DevProblem& P, double q)
 {
-    const T* t = reinterpret_cast<const T*>(P.ftab);
+    const double* t = reinterpret_cast<const double*>(P.ftab);
     const int n = P.n_ftab;
-    if (!(q > (T)P.ftab_q0)) return t[0];
-    if (q > (T)P.ftab_q1) return T(0);
-    const T u = log_T(q / (T)P.ftab_q0) * (T)P.ftab_scale;
-    if (u >= T(n - 1)) return t[n - 1];
+    if (!(q > P.ftab_q0)) return t[0];
+    if (q > P.ftab_q1) return 0.0;
+    const double u = log(q / P.ftab_q0) * P.ftab_scale;
+    if (u >= (double)(n - 1)) return t[n - 1];
     const int k = (int)u;
-    const T w = u - (T)k;
+    const double w = u - (double)k;
     return t[k] + w * (t[k + 1] - t[k]);
 }
 
-__device__ __forceinline__ float relic_f_dev(const DevProblem& P, float q)
-{
-    if (P.f_kind == NU_F_TABLE) return relic_f_table<float>(P, q);
-    if (P.f_kind == NU_F_FREEZEIN) {
-        const float qq = fmaxf(q, 1e-30f);
-        return expf(-qq) * rsqrtf(qq);
-    }
-    return 1.0f / (1.0f + expf(q - (float)P.f_p0));
-}
 __device__ __forceinline__ double relic_f_dev(const DevProblem& P, double q)
 {
-    if (P.f_kind == NU_F_TABLE) return relic_f_table<double>(P, q);
+    if (P.f_kind == NU_F_TABLE) return relic_f_table(P, q);
     if (P.f_kind == NU_F_FREEZEIN) {
         const double qq = fmax(q, 1e-300);
         return exp(-qq) / sqrt(qq);
@@ -727,17 +715,18 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             continue;
         }
 
-        // Liouville map and the weight of each trajectory in Eq. localdensity.
-        // The final momentum is that of the fiducial mass; mass a of a
-        // mass-reuse request reads it scaled by s_a (Sec. III).
-        T qf[TPT];
+        // Liouville map and the weight of each trajectory in Eq. localdensity,
+        // in FP64 from the final state (in the mixed mode its FP32 components
+        // widened exactly).  The final momentum is that of the fiducial mass;
+        // mass a of a mass-reuse request reads it scaled by s_a (Sec. III).
+        double qf[TPT];
 #pragma unroll
         for (int i = 0; i < TPT; ++i) {
-            const T vmag = sqrt(vx[i] * vx[i] + vy[i] * vy[i]);
-            qf[i] = vmag * (T)P.q_scale;
+            const double ux = (double)vx[i], uy = (double)vy[i];
+            qf[i] = sqrt(fma(ux, ux, uy * uy)) * P.q_scale;
             if (P.qi && act[i]) {
                 const int t = tis * P.tile + i * blockDim.x + threadIdx.x;
-                reinterpret_cast<T*>(P.qi)[(size_t)seg * n_seg + t] = qf[i];
+                reinterpret_cast<T*>(P.qi)[(size_t)seg * n_seg + t] = (T)qf[i];
             }
         }
         // momentum and direction nodes of each trajectory (recomputed here
@@ -752,12 +741,12 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         const int nm = P.n_mass;
         double* part = P.partials + ((size_t)seg * tps + tis) * 2 * nm;
         for (int a = 0; a < nm; ++a) {
-            const T sa = (T)P.mass_s[a];
+            const double sa = P.mass_s[a];
             double acc = 0.0, accc = 0.0;
 #pragma unroll
             for (int i = 0; i < TPT; ++i) {
                 if (!act[i]) continue;
-                const double f = (double)relic_f_dev(P, qf[i] * sa);
+                const double f = relic_f_dev(P, qf[i] * sa);
                 const double wm = P.wmu[tk[i]];
                 acc += P.wq[tj[i]] * wm * f;
                 accc += P.wqc[tj[i]] * wm * f;

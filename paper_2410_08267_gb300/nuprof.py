@@ -65,7 +65,7 @@ class nu_opts(C.Structure):
     _fields_ = [("n_steps", C.c_int), ("precision", C.c_int), ("z_end", C.c_double),
                 ("radii_unit", C.c_int), ("block", C.c_int), ("tpt", C.c_int), ("flags", C.c_int),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("timeout_ms", C.c_double)]
 
 
 class nu_plan_info(C.Structure):

@@ -1,29 +1,30 @@
-"""Helpers shared by the GPU test modules: tolerances and the conditioning-aware
-parity criterion.
+"""Helpers shared by the GPU test modules: tolerances and the parity criterion.
 
-Why conditioning matters here.  With a fixed number of RK4 steps the discrete
-map is under-resolved in halo cores (an orbit near r ~ 1 kpc spans a few
-steps), and it amplifies rounding-size differences in the start state by up
-to ~1e10 for the trajectories that pass close to the centre.  Two correct
-FP64 implementations then differ in n/nbar at the innermost radii by about
-as much as the oracle differs from ITSELF when every start velocity is
-perturbed by a few ulps.  The parity criterion therefore is, per radius,
+The stated tolerances on n/nbar are relative: TOL = 1e-5 in the FP64 mode and
+1e-4 in the mixed mode (FP32 state and force, FP64 tables and sums).  Every
+radius is held to TOL.
 
-    |gpu - oracle| / oracle  <=  max(TOL, K * spread)
+Conditioning.  With a fixed number of RK4 steps the discrete map is
+under-resolved in halo cores (an orbit near 1 kpc spans a few steps) and is
+chaotic there: the oracle's own n/nbar at such radii moves when every
+trajectory's state is perturbed by rounding-size noise at every step.  The
+probe measures this `spread`: the largest pairwise relative difference among
+the oracle and five seeded runs of it with noise of relative size EPS (a few
+ulps of the mode's precision) on the start state and on every step's
+increments; for the mixed mode the probe also rounds the state to float32
+after every step, which is what FP32 state storage does to the computation.
 
-where TOL is the stated tolerance (1e-5 FP64, 1e-4 mixed) and `spread` is the
-largest pairwise relative difference among the oracle and five seeded runs of
-it in which every trajectory's start state and every step's increments carry
-independent noise of relative size EPS (a few ulps of the mode's precision);
-for the mixed mode the probe also rounds the oracle's state to float32 after
-every RK4 step, which is what FP32 state storage does to the computation.
-Relics with the non-thermal q^(-1/2) e^(-q) distribution are the worst case:
-f is singular at q = 0, so a trajectory that the under-resolved map brings
-nearly to rest dominates its radius, and n/nbar at core radii moves by 10-50%
-between realizations; for them only well-conditioned radii are compared.  Where the oracle is well conditioned (spread << TOL) this is
-exactly the stated tolerance; strict tests elsewhere check that, on
-well-conditioned trajectories and radii, the FP64 mode matches the oracle to
-1e-10.
+A radius may miss TOL only where the oracle itself is not reproducible to
+that level under the mode's rounding (K x spread > TOL).  Such a radius is a
+MISS against the target: it is printed as one and must lie within
+K x spread, which for a compared radius never exceeds CAP x TOL.  Where
+K x spread exceeds CAP x TOL (the innermost radii of some heavy halos,
+keV-mass freeze-in relics whose n/nbar rests on a few trajectories brought
+nearly to rest, short runs through massive halos) no result of the mode can
+be compared with the oracle at all: such a radius is UNCONDITIONED, is
+printed as such, is only checked to lie within K x spread, and does not count
+as compared; tests require a minimum number of compared radii.  Every check
+prints the bound it applied per radius.
 """
 import itertools
 
@@ -40,6 +41,7 @@ TOL_FP64 = TOL[W.FP64]
 TOL_MIXED = TOL[W.MIXED]
 EPS = {W.FP64: 2.0 ** -50, W.MIXED: 2.0 ** -22}   # ~4 ulp of FP64 / ~2 ulp of FP32
 K = 4.0
+CAP = 10.0          # a conditioned radius is never accepted beyond CAP x TOL
 SEEDS = (1, 2, 3, 4, 5)
 
 
@@ -66,7 +68,7 @@ def oracle_with_spread(pb, sel=None, seeds=SEEDS):
     pairwise relative difference among the oracle and its perturbed runs (each
     pair is two equally valid realizations of the same discrete computation,
     which is what the CUDA result and the oracle are)."""
-    o = oracle.profile(pb, radius_sel=sel)
+    o = oracle.profile(pb.replace(precision=W.FP64), radius_sel=sel)
     eps = EPS[pb.precision]
     runs = [o] + [oracle.profile_perturbed(pb, eps, s, radius_sel=sel, step_noise=True,
                                            round_state=(pb.precision == W.MIXED)) for s in seeds]
@@ -76,19 +78,56 @@ def oracle_with_spread(pb, sel=None, seeds=SEEDS):
     return o, spread
 
 
-def assert_parity(got, pb, sel=None, where="", seeds=SEEDS, conditioned_only=False):
-    """Per-radius conditioning-aware parity; returns (err, bound) on the checked radii.
-    With conditioned_only, radii whose oracle spread exceeds TOL are skipped."""
+def classify(err, spread, tol):
+    """Per radius: 'ok' (err <= tol); 'miss' (tol < err <= K spread <= CAP tol);
+    'unconditioned' (K spread > CAP tol and err <= K spread); or 'FAIL'."""
+    out = []
+    for e, s in zip(err, spread):
+        if e <= tol:
+            out.append("ok")
+        elif e <= K * s <= CAP * tol:
+            out.append("miss")
+        elif K * s > CAP * tol and e <= K * s:
+            out.append("unconditioned")
+        else:
+            out.append("FAIL")
+    return np.array(out)
+
+
+def bound_of(status, spread, tol):
+    return tol if status == "ok" else max(tol, K * spread)
+
+
+def report(where, idx, err, spread, tol, status):
+    print(f"[parity] {where}: tol {tol:.0e}")
+    for i, e, s, st in zip(idx, err, spread, status):
+        print(f"[parity]   radius {int(i):3d}  err {e:.2e}  oracle spread {s:.2e}  "
+              f"bound {bound_of(st, s, tol):.2e}  {st}")
+
+
+def assert_parity(got, pb, sel=None, where="", seeds=SEEDS, conditioned_only=False,
+                  min_checked=0, allow_miss=True):
+    """Per-radius parity at the stated tolerance; returns (err, status) on the
+    checked radii.  conditioned_only skips radii whose oracle spread reaches
+    TOL; allow_miss=False holds every checked radius to TOL without
+    exception.  At least min_checked radii must be compared (not skipped and
+    not unconditioned)."""
     o, spread = oracle_with_spread(pb, sel, seeds)
+    tol = TOL[pb.precision]
     idx = np.arange(pb.n_radii) if sel is None else np.asarray(sel)
     if conditioned_only:
-        idx = idx[spread[idx] < TOL[pb.precision]]
+        idx = idx[spread[idx] < tol]
     err = rel_err(np.asarray(got)[idx], o[idx])
-    bound = np.maximum(TOL[pb.precision], K * spread[idx])
-    bad = err > bound
-    assert not np.any(bad), (f"{where} radii {idx[bad]}: err {err[bad]} > bound {bound[bad]} "
-                             f"(oracle spread {spread[idx][bad]})")
-    return err, bound
+    status = classify(err, spread[idx], tol)
+    if not allow_miss:
+        status = np.where(status == "ok", "ok", "FAIL")
+    report(where, idx, err, spread[idx], tol, status)
+    bad = status == "FAIL"
+    assert not np.any(bad), (f"{where} radii {idx[bad]}: err {err[bad]} "
+                             f"(tol {tol:.0e}, oracle spread {spread[idx][bad]})")
+    n_compared = int(np.sum((status == "ok") | (status == "miss")))
+    assert n_compared >= min_checked, f"{where}: only {n_compared} radii could be compared"
+    return err, status
 
 
 def run_handle(pb, **kw):
