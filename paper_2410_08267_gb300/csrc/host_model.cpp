@@ -57,6 +57,7 @@ int validate(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* relic,
     if (o->n_steps < 1) return NU_EINVAL;
     if (o->n_steps > NU_MAX_STEPS) return NU_ENOTSUP;
     if (o->precision != NU_FP64 && o->precision != NU_MIXED) return NU_EINVAL;
+    if ((o->flags & NU_FLAG_VERIFY) && o->precision != NU_MIXED) return NU_EINVAL;
     if (o->radii_unit != NU_RADII_KPC && o->radii_unit != NU_RADII_R200) return NU_EINVAL;
     if (o->radii_unit == NU_RADII_R200 && halo->M_h == 0.0) return NU_EINVAL;
     if (o->block < 64 || o->block > 512 || (o->block % 32) != 0) return NU_EINVAL;
@@ -198,11 +199,17 @@ void coef_table_into(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& 
         t[C_T0] = Sa / d.Ic;
         t[C_T1] = Sm / d.Ic;
         t[C_T2] = Sb / d.Ic;
-        t[C_PAD] = 0.0;
+        t[C_IREM] = h / 6.0 * (Aa + 4.0 * Am + Ab);    // this step's share, summed below
         Aa = Ab;
         BFa = BFb;
         Sa = Sb;
         Qa = Qb;
+    }
+    // remaining free-streaming distance per unit speed from each step to the end
+    double rem = 0.0;
+    for (int n = n_steps - 1; n >= 0; --n) {
+        rem += tab[(size_t)n * C_COUNT + C_IREM];
+        tab[(size_t)n * C_COUNT + C_IREM] = rem;
     }
 }
 

@@ -38,7 +38,9 @@ enum CoefSlot {
     C_T0,        // S(z_a) / I(c)        with rs = S/r: y = r^2 rs, S^2/(I(c) r) = rs T
     C_T1,
     C_T2,
-    C_PAD,       // zero (keeps a step at a multiple of 16 bytes)
+    C_IREM,      // sum over steps k >= n of (h/6)(A_a + 4 A_m + A_b): the comoving
+                 // distance per unit speed that a force-free trajectory covers from
+                 // the start of step n to z_end (App. B's I_io, for the discrete map)
     C_COUNT
 };
 static_assert(C_COUNT == 20, "coefficient table layout");
@@ -132,6 +134,12 @@ int profile_n_out(const nu_profile* h);   // n_mass * n_radii result values
 int profile_n_steps(const nu_profile* h);
 long long profile_n_traj(const nu_profile* h);
 int profile_read(const nu_profile* h, double* out, double* err, void* stream);
+// NU_FLAG_VERIFY: the FP64 twin of a handle (nullptr without the flag), a
+// launch of the twin alone with an event after it, and a query of that event
+// (NU_OK done, NU_EAGAIN running, NU_EBUSY never run, NU_ECUDA).
+nu_profile* profile_twin(const nu_profile* h);
+int profile_twin_run(nu_profile* h, void* stream);
+int profile_twin_query(const nu_profile* h);
 
 // Kernel launch helpers (traj_kernel.cu).
 int launch_traj(int precision, int tpt, int block, int grid, size_t smem_bytes,

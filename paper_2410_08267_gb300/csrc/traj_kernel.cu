@@ -117,21 +117,28 @@ constexpr float kR2Guard = 1e-20f;
 // A trajectory is finished when its velocity can no longer change: it lies
 // beyond R, where the gradient is exactly zero (mass compensation, App. A),
 // and the straight line it follows from there along the integration direction
-// (-v: the backward step moves it along -v) never comes back within R.  That
-// holds when it recedes (x . v <= 0), or when the line's closest approach to
-// the centre, b^2 = r^2 - (x . v)^2 / v^2, stays beyond R (App. B's criterion
-// for rays that miss the halo, here exact because nothing acts outside R).
-// The factor kMiss on R^2 keeps the test safe against the rounding of the
-// stepped positions (relative deviations below 1e-4 from the straight line).
+// (-v: the backward step moves it along -v) does not come back within R
+// before z_end.  That holds when it recedes (x . v <= 0); when the line's
+// closest approach to the centre, b^2 = r^2 - (x . v)^2 / v^2, stays beyond R
+// (App. B's first criterion, for rays that miss the halo); or when the
+// trajectory is too slow to cover the distance r - R before z_end (App. B's
+// second criterion, v I_io < r - R), with irem the remaining force-free
+// distance per unit speed of the discrete map.  All three are exact here
+// because nothing acts outside R.  The factor kMiss keeps the tests safe
+// against the rounding of the stepped positions (relative deviations below
+// 1e-4 from the straight line).
 template <typename T>
-__device__ __forceinline__ bool escapes(T r2, T dot, T v2, T R2)
+__device__ __forceinline__ bool escapes(T r2, T dot, T v2, T R2, T R, T irem)
 {
     const T kMiss = T(1.001);
-    return r2 >= R2 && (dot <= T(0) || (r2 - kMiss * R2) * v2 >= dot * dot);
+    if (!(r2 >= R2)) return false;
+    if (dot <= T(0) || (r2 - kMiss * R2) * v2 >= dot * dot) return true;
+    const T reach = R + sqrt(v2) * irem;          // farthest start that still reaches R
+    return r2 >= kMiss * (reach * reach);
 }
 
-struct HaloF32 { float invIc, invR3, R2; };
-struct HaloF64 { double invIc, invR3, R2; };
+struct HaloF32 { float invIc, invR3, R2, R; };
+struct HaloF64 { double invIc, invR3, R2, R; };
 
 // Branch tallies of force evaluations, kept only by the counting variant of the
 // kernel (used once, untimed, to turn the data-dependent work into an exact
@@ -234,14 +241,14 @@ template <> struct PrecTraits<float> {
     using Halo = HaloF32;
     static __device__ __forceinline__ Halo halo(const DevProblem& P)
     {
-        return {(float)P.invIc, (float)P.invR3, (float)P.R2};
+        return {(float)P.invIc, (float)P.invR3, (float)P.R2, (float)sqrt(P.R2)};
     }
 };
 template <> struct PrecTraits<double> {
     using Halo = HaloF64;
     static __device__ __forceinline__ Halo halo(const DevProblem& P)
     {
-        return {P.invIc, P.invR3, P.R2};
+        return {P.invIc, P.invR3, P.R2, sqrt(P.R2)};
     }
 };
 
@@ -658,8 +665,9 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                     const f2 r2 = fma2(X, X, mul2(Y, Y));
                     const f2 dot = fma2(X, VX, mul2(Y, VY));
                     const f2 v2 = fma2(VX, VX, mul2(VY, VY));
-                    const bool fin0 = !act[0] || escapes(f2lo(r2), f2lo(dot), f2lo(v2), hc.R2);
-                    const bool fin1 = !act[1] || escapes(f2hi(r2), f2hi(dot), f2hi(v2), hc.R2);
+                    const float irem = tab[(size_t)n * 2 * C_COUNT + 2 * C_IREM];
+                    const bool fin0 = !act[0] || escapes(f2lo(r2), f2lo(dot), f2lo(v2), hc.R2, hc.R, irem);
+                    const bool fin1 = !act[1] || escapes(f2hi(r2), f2hi(dot), f2hi(v2), hc.R2, hc.R, irem);
                     done |= fin0 && fin1;
                     if (__all_sync(0xffffffffu, done)) break;
                 }
@@ -681,7 +689,8 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                     for (int i = 0; i < TPT; ++i) {
                         fin_i[i] = !act[i] || escapes(fma(x[i], x[i], y[i] * y[i]),
                                                       fma(x[i], vx[i], y[i] * vy[i]),
-                                                      fma(vx[i], vx[i], vy[i] * vy[i]), hc.R2);
+                                                      fma(vx[i], vx[i], vy[i] * vy[i]), hc.R2,
+                                                      hc.R, tab[(size_t)n * C_COUNT + C_IREM]);
                         fin &= fin_i[i];
                     }
                     done |= fin;

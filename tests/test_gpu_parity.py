@@ -241,6 +241,41 @@ def test_rays_that_miss_the_halo_stop_at_once(prec):
     assert live_far < 0.6 * pb.traj_steps, (live_far, pb.traj_steps)
 
 
+@pytest.mark.parametrize("prec", [W.FP64, W.MIXED])
+def test_slow_trajectories_beyond_R_stop_at_once(prec):
+    """App. B's velocity cutoff: beyond R a trajectory too slow to cover r - R
+    before z_end keeps its momentum.  A momentum grid whose fastest speed
+    covers only R/4 by z_end (App. B's I_io taken here by quadrature of
+    (1+z)/H), at 1.5 R, 4 R and 20 R, with directions that point into the
+    halo: every trajectory is finished at the first test, so the counting run
+    integrates no step at all, while q_i and n/nbar equal the oracle's full
+    integration (q_i is the start momentum, n/nbar is 1)."""
+    from scipy import integrate
+    pb0 = W.plain_small(precision=prec)[0]
+    R = oracle.derive(pb0)["R"]
+    I_io = integrate.quad(lambda z: (1.0 + z) / oracle.H(pb0, z), 0.0, pb0.z_end)[0]
+    v_max = 0.25 * R / I_io                                  # km/s
+    q_max = v_max * pb0.m_eV / (299792.458 * 8.617333262e-5 * pb0.T0_K)
+    pb = pb0.replace(radii=np.array([1.5, 4.0, 20.0]) * R, n_q=24, q_min=q_max / 100.0,
+                     q_max=q_max, n_mu=16, n_steps=200)
+    got = _qi(pb)
+    _, ref = oracle.profile(pb, return_qi=True)
+    q0 = oracle.log_grid(pb.n_q, pb.q_min, pb.q_max)[0]
+    tol_q = 1e-14 if prec == W.FP64 else 1e-6
+    assert np.allclose(ref, q0[None, :, None], rtol=1e-14, atol=0.0)   # the oracle integrates all
+    assert np.allclose(got, ref, rtol=tol_q, atol=0.0)
+    out = nu.profile(pb)[0]
+    assert np.all(np.abs(out - 1.0) < (1e-13 if prec == W.FP64 else 1e-6))
+    h = nu.create(pb)
+    b = nu.nu_batch_create([h])
+    try:
+        c = nu.nu_batch_branch_counts(b)
+    finally:
+        nu.nu_batch_destroy(b)
+        nu.nu_profile_destroy(h)
+    assert c[4] == 0, c
+
+
 @pytest.mark.parametrize("prec, steps, tpt", [(W.MIXED, nu.NU_MAX_STEPS, 3), (W.MIXED, nu.NU_MAX_STEPS, 1),
                                               (W.FP64, 2000, 1)])
 def test_tables_too_large_for_shared_memory_are_read_through_l1(prec, steps, tpt):
