@@ -97,7 +97,8 @@ extern "C" {
 /* ---- precision modes ------------------------------------------------------ */
 #define NU_FP64   0        /* state, force, f and sums in FP64                 */
 #define NU_MIXED  1        /* FP32 state and force; time from an FP64-built
-                              table; f in FP32; quadrature sums in FP64        */
+                              table; Liouville map, f and quadrature sums in
+                              FP64                                             */
 
 /* ---- radius units ---------------------------------------------------------- */
 #define NU_RADII_KPC   0   /* comoving kpc                                     */
@@ -114,6 +115,14 @@ extern "C" {
                               staging it in shared memory (frees shared memory,
                               so more CTAs fit on an SM); results are identical.
                               A table larger than 227 KB is always read this way */
+#define NU_FLAG_VERIFY  16 /* mixed precision only: the request is also run in
+                              the FP64 mode (same grids and steps) on the GPU,
+                              and err_est then reports, per result, the error
+                              against FP64, |mixed - FP64| / |FP64|, instead of
+                              the quadrature self-estimate.  Costs an FP64 run
+                              (about 100x the mixed kernel's time) and its
+                              device memory; works for runs, batches and
+                              served requests                                  */
 
 typedef struct nu_cosmo {
     double Om;       /* matter density today; Omega_Lambda = 1 - Om (Sec. II.A) */
@@ -242,8 +251,9 @@ NU_API int nu_profile_run(nu_profile* h, void* stream);
 
 /* Wait for the last run of `h` and copy n/nbar (and, if err_est != NULL, an
  * estimate of the relative quadrature error of each value: the difference to
- * the same sum on a grid with every other q node, divided by 3) into host
- * arrays of n_radii doubles.  For a request with several masses (nu_relic
+ * the same sum on a grid with every other q node, divided by 3; for a request
+ * created with NU_FLAG_VERIFY, the relative difference to the same request in
+ * the FP64 mode) into host arrays of n_radii doubles.  For a request with several masses (nu_relic
  * n_masses > 0) the arrays hold [n_masses][n_radii] values and n_radii must be
  * n_masses times the number of radii.  Errors: NU_EBUSY (never run), NU_EINVAL
  * (size mismatch), NU_EDEVICE (non-finite sum), NU_ECUDA. */
@@ -384,7 +394,9 @@ typedef struct nu_serve_stats {
 /* Start a server on the current device.  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
 NU_API int nu_server_create(const nu_server_opts* opts, nu_server** out);
 /* Queue a request (arguments as for nu_profile_create; opts may be NULL and
- * only its n_steps, z_end and radii_unit are used).  Returns a ticket at once;
+ * only its n_steps, z_end, radii_unit and NU_FLAG_VERIFY are used: a verified
+ * request's FP64 run goes on a stream of its own, and the request is
+ * delivered, with its error against FP64 in err_est, when both are done).  Returns a ticket at once;
  * the request is validated first (NU_EINVAL / NU_ENOTSUP), and a request that
  * can never fit the budget later completes with NU_ENOMEM. */
 NU_API int nu_server_submit(nu_server* s, const nu_cosmo* cosmo, const nu_halo* halo,

@@ -115,6 +115,7 @@ struct nu_profile {
     int* d_prefix = nullptr;
     unsigned* d_ctrl = nullptr;     // [0] tile counter, [1] status
     std::shared_ptr<RunEvent> last;
+    nu_profile* twin = nullptr;     // NU_FLAG_VERIFY: the same request in the FP64 mode
 };
 
 struct nu_batch {
@@ -170,6 +171,14 @@ int plan_common(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic* reli
                                      relic_n_mass(*relic),
                                      relic->f_kind == NU_F_TABLE ? relic->n_table : 0,
                                      &info.h2d_bytes);
+    if (o.flags & NU_FLAG_VERIFY) {   // the FP64 twin's buffers come from the same allocator
+        long long twin_h2d = 0;
+        info.device_bytes += device_bytes(NU_FP64, o.n_steps, n_radii, grid->n_q, grid->n_mu,
+                                          tps_alloc, false, relic_n_mass(*relic),
+                                          relic->f_kind == NU_F_TABLE ? relic->n_table : 0,
+                                          &twin_h2d);
+        info.h2d_bytes += twin_h2d;
+    }
     const long long nt = (long long)tiles_per_seg * n_radii;
     if (nt > (1LL << 30)) return NU_EINVAL;
     info.n_tiles = (int)nt;
@@ -237,11 +246,60 @@ private:
     unsigned char* p_ = nullptr;
 };
 
+// Enqueue one handle's own launch (work counter and status cleared first).
+int launch_profile(nu_profile* h, cudaStream_t s)
+{
+    int grid = 0;
+    const bool gtab = (h->opts.flags & NU_FLAG_GTAB) != 0;
+    int rc = persistent_grid(h->opts.precision, h->opts.tpt, h->opts.block, h->smem, h->n_tiles, &grid,
+                             gtab);
+    if (rc != NU_OK) return rc;
+    if (cudaMemsetAsync(h->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    return launch_traj(h->opts.precision, h->opts.tpt, h->opts.block, grid, h->smem, h->d_prob,
+                       h->d_prefix, 1, h->n_tiles, h->d_ctrl, s, gtab);
+}
+
+// err = |mixed - fp64| / |fp64| per result (0 where both are 0)
+void verified_error(const double* mixed, const double* fp64, double* err, int n)
+{
+    for (int i = 0; i < n; ++i) {
+        const double d = std::fabs(mixed[i] - fp64[i]);
+        err[i] = d == 0.0 ? 0.0 : d / std::fabs(fp64[i]);
+    }
+}
+
 }  // namespace
 
 namespace nuprof {
 
 const DevProblem& profile_desc(const nu_profile* h) { return h->hdp; }
+nu_profile* profile_twin(const nu_profile* h) { return h->twin; }
+int profile_twin_run(nu_profile* h, void* stream)
+{
+    if (!h->twin) return NU_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int rc = launch_profile(h->twin, s);
+    if (rc != NU_OK) return rc;
+    auto ev = std::make_shared<RunEvent>();
+    if (!ev->ev || cudaEventRecord(ev->ev, s) != cudaSuccess) {
+        cudaGetLastError();
+        return NU_ECUDA;
+    }
+    h->twin->last = ev;
+    return NU_OK;
+}
+int profile_twin_query(const nu_profile* h)
+{
+    if (!h->twin || !h->twin->last) return NU_EBUSY;
+    const cudaError_t e = cudaEventQuery(h->twin->last->ev);
+    if (e == cudaSuccess) return NU_OK;
+    if (e == cudaErrorNotReady) return NU_EAGAIN;
+    cudaGetLastError();
+    return NU_ECUDA;
+}
 int profile_n_radii(const nu_profile* h) { return h->n_radii; }
 int profile_n_out(const nu_profile* h) { return h->n_radii * h->hdp.n_mass; }
 int profile_n_steps(const nu_profile* h) { return h->opts.n_steps; }
@@ -262,6 +320,18 @@ int profile_read(const nu_profile* h, double* out, double* err, void* stream)
     }
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(out[i])) return NU_EDEVICE;
+    if (h->twin && err) {                 // verified: the error against the FP64 run
+        std::vector<double> ref((size_t)n);
+        if (cudaMemcpyAsync(ref.data(), h->twin->hdp.out, bytes, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return NU_ECUDA;
+        }
+        for (int i = 0; i < n; ++i)
+            if (!std::isfinite(ref[i])) return NU_EDEVICE;
+        verified_error(out, ref.data(), err, n);
+    }
     return NU_OK;
 }
 
@@ -479,6 +549,18 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     h->d_prob = reinterpret_cast<DevProblem*>(base + o_prob);
     h->d_prefix = reinterpret_cast<int*>(base + o_pref);
     h->d_ctrl = reinterpret_cast<unsigned*>(base + o_ctrl);
+    if (o.flags & NU_FLAG_VERIFY) {       // the same request in the FP64 mode
+        nu_opts o2 = o;
+        o2.precision = NU_FP64;
+        o2.flags = 0;
+        o2.block = 256;
+        o2.tpt = 1;
+        rc = nu_profile_create(cosmo, halo, relic, radii, n_radii, p_grid, &o2, &h->twin);
+        if (rc != NU_OK) {
+            h->mem.release();
+            return rc;
+        }
+    }
     *out = h.release();
     return NU_OK;
 }
@@ -487,17 +569,8 @@ int nu_profile_run(nu_profile* h, void* stream)
 {
     if (!h) return NU_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    int grid = 0;
-    const bool gtab = (h->opts.flags & NU_FLAG_GTAB) != 0;
-    int rc = persistent_grid(h->opts.precision, h->opts.tpt, h->opts.block, h->smem, h->n_tiles, &grid,
-                             gtab);
-    if (rc != NU_OK) return rc;
-    if (cudaMemsetAsync(h->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess) {
-        cudaGetLastError();
-        return NU_ECUDA;
-    }
-    rc = launch_traj(h->opts.precision, h->opts.tpt, h->opts.block, grid, h->smem, h->d_prob,
-                     h->d_prefix, 1, h->n_tiles, h->d_ctrl, stream, gtab);
+    int rc = launch_profile(h, s);
+    if (rc == NU_OK && h->twin) rc = launch_profile(h->twin, s);
     if (rc != NU_OK) return rc;
     auto ev = std::make_shared<RunEvent>();
     if (!ev->ev || cudaEventRecord(ev->ev, s) != cudaSuccess) {
@@ -530,7 +603,18 @@ int nu_profile_result(nu_profile* h, double* n_over_nbar, double* err_est, int n
     for (int i = 0; i < n_radii; ++i)
         if (!std::isfinite(tmp[i])) return NU_EDEVICE;
     std::memcpy(n_over_nbar, tmp, n_radii * sizeof(double));
-    if (err_est) std::memcpy(err_est, tmp + n_radii, n_radii * sizeof(double));
+    if (err_est && h->twin) {             // verified: the error against the FP64 run
+        if (cudaMemcpy(tmp + n_radii, h->twin->hdp.out, n_radii * sizeof(double),
+                       cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return NU_ECUDA;
+        }
+        for (int i = 0; i < n_radii; ++i)
+            if (!std::isfinite(tmp[n_radii + i])) return NU_EDEVICE;
+        verified_error(n_over_nbar, tmp + n_radii, err_est, n_radii);
+    } else if (err_est) {
+        std::memcpy(err_est, tmp + n_radii, n_radii * sizeof(double));
+    }
     return NU_OK;
 }
 
@@ -594,6 +678,7 @@ void nu_profile_destroy(nu_profile* h)
     if (!h) return;
     if (h->last) cudaEventSynchronize(h->last->ev);
     h->last.reset();
+    nu_profile_destroy(h->twin);
     h->mem.release();
     delete h;
 }
@@ -690,10 +775,12 @@ static int batch_enqueue(nu_batch* b, cudaStream_t s, bool timed)
 {
     if (cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return NU_ECUDA;
     if (timed && cudaEventRecord(b->t0, s) != cudaSuccess) return NU_ECUDA;
-    const int rc = launch_traj(b->precision, b->tpt, b->block, b->grid, b->smem, b->d_probs,
-                               b->d_prefix, (int)b->hs.size(), b->n_tiles, b->d_ctrl, s, b->gtab);
+    int rc = launch_traj(b->precision, b->tpt, b->block, b->grid, b->smem, b->d_probs,
+                         b->d_prefix, (int)b->hs.size(), b->n_tiles, b->d_ctrl, s, b->gtab);
     if (rc != NU_OK) return rc;
     if (timed && cudaEventRecord(b->t1, s) != cudaSuccess) return NU_ECUDA;
+    for (nu_profile* h : b->hs)           // verified requests: their FP64 runs follow
+        if (h->twin && (rc = launch_profile(h->twin, s)) != NU_OK) return rc;
     return NU_OK;
 }
 

@@ -141,6 +141,7 @@ struct Active {
     int n_steps;
     bool cancelled;
     Clock::time_point t_submit;
+    Clock::time_point t_ready;    // verified requests: when the mixed result was ready
 };
 
 struct Done {
@@ -157,6 +158,7 @@ struct nu_server {
     void* block = nullptr;                  // the arena's device memory
     Arena arena;
     cudaStream_t compute = nullptr, upload = nullptr;
+    cudaStream_t verify = nullptr;          // FP64 runs of verified requests
     cudaEvent_t ev = nullptr;
     DevProblem* d_desc[2] = {nullptr, nullptr};   // per-iteration descriptors (double buffer)
     int* d_prefix[2] = {nullptr, nullptr};
@@ -171,6 +173,7 @@ struct nu_server {
     std::map<long long, bool> cancel_requests;
     std::vector<Active> active;             // on the GPU (the launch in flight)
     std::vector<Active> staged;             // admitted, join the next launch
+    std::vector<Active> verifying;          // mixed result ready, FP64 run still going
     std::atomic<int> on_device{0};          // active + staged, for statistics
     long long next_ticket = 1;
     bool stop = false;
@@ -186,6 +189,7 @@ struct nu_server {
 
     void run();
     bool admit_one();
+    void deliver_verified();
     double staged_work() const
     {
         double w = 0.0;
@@ -278,6 +282,13 @@ bool nu_server::admit_one()
             h = nullptr;
         }
     }
+    if (rc == NU_OK && profile_twin(h)) {     // a verified request: its FP64 run starts now
+        rc = profile_twin_run(h, verify);
+        if (rc != NU_OK) {
+            nu_profile_destroy(h);
+            h = nullptr;
+        }
+    }
     std::lock_guard<std::mutex> g(mu);
     pending.pop_front();
     if (rc != NU_OK) {
@@ -286,10 +297,34 @@ bool nu_server::admit_one()
         ++rejected;
         return true;
     }
-    staged.push_back(Active{p.ticket, h, state, 0, profile_n_steps(h), false, p.t_submit});
+    staged.push_back(Active{p.ticket, h, state, 0, profile_n_steps(h), false, p.t_submit, {}});
     ++admitted;
     on_device.store((int)(active.size() + staged.size()));
     return true;
+}
+
+// Deliver verified requests whose FP64 run has finished (bounded: one that
+// does not finish within gpu_timeout_ms of its mixed result fails with
+// NU_ETIMEDOUT, and its memory is leaked rather than freed under a kernel).
+void nu_server::deliver_verified()
+{
+    for (size_t i = 0; i < verifying.size();) {
+        Active& a = verifying[i];
+        const int q = profile_twin_query(a.h);
+        if (q == NU_EAGAIN && ms_since(a.t_ready) <= o.gpu_timeout_ms) {
+            ++i;
+            continue;
+        }
+        if (q == NU_OK) {
+            const int nr = profile_n_out(a.h);
+            std::vector<double> out(nr), err(nr);
+            const int r = profile_read(a.h, out.data(), err.data(), upload);
+            finish(a, r, &out, &err);
+        } else {
+            record(a, q == NU_EAGAIN ? NU_ETIMEDOUT : q, nullptr, nullptr);
+        }
+        verifying.erase(verifying.begin() + i);
+    }
 }
 
 void nu_server::run()
@@ -304,9 +339,10 @@ void nu_server::run()
             std::unique_lock<std::mutex> lk(mu);
             if (stop) return;
             if (active.empty() && staged.empty() && pending.empty())
-                cv.wait_for(lk, std::chrono::milliseconds(20));
+                cv.wait_for(lk, std::chrono::milliseconds(verifying.empty() ? 20 : 1));
             if (stop) return;
         }
+        deliver_verified();
         // with nothing on the GPU, admit requests up to one launch's budget
         // before launching (the rest are admitted while it runs)
         if (active.empty()) {
@@ -362,7 +398,7 @@ void nu_server::run()
             d.step_end = std::min(a.n_steps, a.progress + (chunk > 0 ? chunk : a.n_steps));
             d.done_count = nullptr;
             d.done_flag = nullptr;
-            if (h_flags && d.step_end == a.n_steps) {
+            if (h_flags && d.step_end == a.n_steps && !profile_twin(a.h)) {
                 h_flags[i] = 0u;
                 d.done_count = d_counts + i;
                 d.done_flag = d_flags + i;
@@ -418,6 +454,7 @@ void nu_server::run()
                 std::lock_guard<std::mutex> g(mu);
                 ++early;
             }
+            deliver_verified();
             // poll closely at first (short launches finish within a few ms and a
             // sleep would add its granularity to every chunk), then back off
             if (!admit_one()) {
@@ -476,6 +513,11 @@ void nu_server::run()
                 release(a);
                 continue;
             }
+            if (profile_twin(a.h)) {              // delivered when its FP64 run is done
+                a.t_ready = Clock::now();
+                verifying.push_back(a);
+                continue;
+            }
             const int nr = profile_n_out(a.h);
             std::vector<double> out(nr), err(nr);
             const int r = profile_read(a.h, out.data(), err.data(), upload);
@@ -531,6 +573,7 @@ int nu_server_create(const nu_server_opts* opts, nu_server** out)
     auto fail = [&](int rc) {
         if (s->compute) cudaStreamDestroy(s->compute);
         if (s->upload) cudaStreamDestroy(s->upload);
+        if (s->verify) cudaStreamDestroy(s->verify);
         if (s->ev) cudaEventDestroy(s->ev);
         if (o.alloc) {
             if (o.free) o.free(s->block, o.device_bytes, o.alloc_ctx);
@@ -554,6 +597,7 @@ int nu_server_create(const nu_server_opts* opts, nu_server** out)
     }
     if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->verify, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (s->h_flags) cudaFreeHost(s->h_flags);
@@ -580,6 +624,7 @@ int nu_server_submit(nu_server* s, const nu_cosmo* cosmo, const nu_halo* halo, c
         p.opts.n_steps = opts->n_steps;
         p.opts.z_end = opts->z_end;
         p.opts.radii_unit = opts->radii_unit;
+        p.opts.flags = opts->flags & NU_FLAG_VERIFY;
     }
     p.opts.precision = s->o.precision;
     p.opts.block = s->o.block;
@@ -697,7 +742,8 @@ void nu_server_destroy(nu_server* s)
     const bool gpu_ok = s->fatal != NU_ETIMEDOUT;
     if (gpu_ok) {
         cudaStreamSynchronize(s->compute);
-        for (auto* list : {&s->active, &s->staged})
+        cudaStreamSynchronize(s->verify);
+        for (auto* list : {&s->active, &s->staged, &s->verifying})
             for (auto& a : *list) {
                 nu_profile_destroy(a.h);
                 s->arena.release(a.state);
@@ -715,6 +761,7 @@ void nu_server_destroy(nu_server* s)
     }
     cudaStreamDestroy(s->compute);
     cudaStreamDestroy(s->upload);
+    cudaStreamDestroy(s->verify);
     cudaEventDestroy(s->ev);
     delete s;
 }

@@ -25,7 +25,7 @@ NU_ETOOBIG = -10
 NU_NOALLOC_MAX_BYTES = 4 << 20
 NU_FP64, NU_MIXED = 0, 1
 NU_RADII_KPC, NU_RADII_R200 = 0, 1
-NU_FLAG_KEEP_QI, NU_FLAG_GRAPH, NU_FLAG_TIMING, NU_FLAG_GTAB = 1, 2, 4, 8
+NU_FLAG_KEEP_QI, NU_FLAG_GRAPH, NU_FLAG_TIMING, NU_FLAG_GTAB, NU_FLAG_VERIFY = 1, 2, 4, 8, 16
 NU_MAX_STEPS = 3000
 NU_MAX_MASSES = 64
 NU_MAX_FTABLE = 4096
@@ -275,8 +275,9 @@ def nu_server_create(device_bytes: int, precision: int = NU_MIXED, max_active: i
     return srv
 
 
-def nu_server_submit(srv, pb: "W.Problem") -> int:
-    cosmo, halo, relic, radii, grid, opts = structs(pb, torch_alloc=False)
+def nu_server_submit(srv, pb: "W.Problem", flags: int = 0) -> int:
+    """Queue a request; flags may hold NU_FLAG_VERIFY."""
+    cosmo, halo, relic, radii, grid, opts = structs(pb, torch_alloc=False, flags=flags)
     t = C.c_longlong()
     _check(lib().nu_server_submit(srv, C.byref(cosmo), C.byref(halo), C.byref(relic), _dptr(radii),
                                   len(radii), C.byref(grid), C.byref(opts), C.byref(t)),

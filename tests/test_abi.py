@@ -166,3 +166,16 @@ def test_tabulated_distribution_validation():
     with pytest.raises(nu.NuError) as e:
         nu.nu_profile_compute_noalloc(cosmo, halo, relic, radii, grid, None)
     assert e.value.code == nu.NU_ENOTSUP
+
+
+def test_verify_rules():
+    """NU_FLAG_VERIFY: the FP64 twin's memory is planned with the request, and
+    the flag needs the mixed mode."""
+    pb = W.plain_small(precision=W.MIXED)[0]
+    plain = nu.plan(pb)
+    verified = nu.plan(pb, flags=nu.NU_FLAG_VERIFY)
+    fp64 = nu.plan(pb.replace(precision=W.FP64))
+    assert verified["device_bytes"] > plain["device_bytes"] + 0.9 * fp64["device_bytes"]
+    with pytest.raises(nu.NuError) as e:
+        nu.plan(pb.replace(precision=W.FP64), flags=nu.NU_FLAG_VERIFY)
+    assert e.value.code == nu.NU_EINVAL
