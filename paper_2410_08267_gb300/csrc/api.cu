@@ -508,43 +508,45 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     P.precision = o.precision;
     P.n_mass = nm;
 
-    Stage staging(upload_end);
-    unsigned char* stage = staging.data();
-    std::memset(stage, 0, upload_end);
-    std::memcpy(stage + o_prob, &P, sizeof(P));
-    const int prefix[2] = {0, h->n_tiles};
-    std::memcpy(stage + o_pref, prefix, sizeof(prefix));
-    if (fp64) {
-        put<double>(stage, o_coef, coef.data(), coef.size());
-        put<double>(stage, o_x0, x0.data(), n_radii);
-        put<double>(stage, o_v0, v0.data(), nq);
-        put<double>(stage, o_mu, mu.data(), nmu);
-        put<double>(stage, o_smu, smu.data(), nmu);
-    } else {
-        put<float>(stage, o_coef, coef.data(), coef.size());
-        float* c2 = reinterpret_cast<float*>(stage + o_coef2);
-        for (size_t i = 0; i < coef.size(); ++i) c2[2 * i] = c2[2 * i + 1] = (float)coef[i];
-        put<float>(stage, o_x0, x0.data(), n_radii);
-        put<float>(stage, o_v0, v0.data(), nq);
-        put<float>(stage, o_mu, mu.data(), nmu);
-        put<float>(stage, o_smu, smu.data(), nmu);
-    }
-    put<double>(stage, o_wq, wq.data(), nq);
-    put<double>(stage, o_wqc, wqc.data(), nq);
-    put<double>(stage, o_wmu, wmu.data(), nmu);
-    put<double>(stage, o_mass, mass_s.data(), nm);
-    put<double>(stage, o_mass + nm * sizeof(double), norms.data(), 2 * (size_t)nm);
-    if (nft > 0) {
-        put<double>(stage, o_ftab, relic->f_table, nft);
-    }
+    {   // the page-locked staging buffer is held (under its lock) only for the upload
+        Stage staging(upload_end);
+        unsigned char* stage = staging.data();
+        std::memset(stage, 0, upload_end);
+        std::memcpy(stage + o_prob, &P, sizeof(P));
+        const int prefix[2] = {0, h->n_tiles};
+        std::memcpy(stage + o_pref, prefix, sizeof(prefix));
+        if (fp64) {
+            put<double>(stage, o_coef, coef.data(), coef.size());
+            put<double>(stage, o_x0, x0.data(), n_radii);
+            put<double>(stage, o_v0, v0.data(), nq);
+            put<double>(stage, o_mu, mu.data(), nmu);
+            put<double>(stage, o_smu, smu.data(), nmu);
+        } else {
+            put<float>(stage, o_coef, coef.data(), coef.size());
+            float* c2 = reinterpret_cast<float*>(stage + o_coef2);
+            for (size_t i = 0; i < coef.size(); ++i) c2[2 * i] = c2[2 * i + 1] = (float)coef[i];
+            put<float>(stage, o_x0, x0.data(), n_radii);
+            put<float>(stage, o_v0, v0.data(), nq);
+            put<float>(stage, o_mu, mu.data(), nmu);
+            put<float>(stage, o_smu, smu.data(), nmu);
+        }
+        put<double>(stage, o_wq, wq.data(), nq);
+        put<double>(stage, o_wqc, wqc.data(), nq);
+        put<double>(stage, o_wmu, wmu.data(), nmu);
+        put<double>(stage, o_mass, mass_s.data(), nm);
+        put<double>(stage, o_mass + nm * sizeof(double), norms.data(), 2 * (size_t)nm);
+        if (nft > 0) {
+            put<double>(stage, o_ftab, relic->f_table, nft);
+        }
 
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
-    if (cudaMemcpyAsync(base, stage, upload_end, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(base + o_cnt, 0, (size_t)n_radii * sizeof(unsigned), s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {   // the staging buffer is reused after this
-        cudaGetLastError();
-        h->mem.release();
-        return NU_ECUDA;
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
+        if (cudaMemcpyAsync(base, stage, upload_end, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(base + o_cnt, 0, (size_t)n_radii * sizeof(unsigned), s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {   // the staging buffer is reused after this
+            cudaGetLastError();
+            h->mem.release();
+            return NU_ECUDA;
+        }
     }
     h->d_prob = reinterpret_cast<DevProblem*>(base + o_prob);
     h->d_prefix = reinterpret_cast<int*>(base + o_pref);
