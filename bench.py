@@ -61,11 +61,11 @@ SMS, FP32_LANES_PER_SM = 152, 128
 # (dram__bytes_read.sum + dram__bytes_write.sum), recorded in
 # profiles/traj_kernel_precision_sweep_mixed.md.  Must be reset to None
 # whenever the kernel changes, until it is captured again.
-NCU_TRAFFIC_BYTES = {"128x3xg": None}
+NCU_TRAFFIC_BYTES = {"128x3xg": 1289472.0}
 # Pipe utilisation of the same kernel and shape on this workload, from one-pass
 # ncu captures (sm__pipe_fma_cycles_active, smsp__issue_active), also recorded
 # in that profile summary; reset together with the traffic when the kernel changes.
-NCU_PIPES = {"128x3xg": None}
+NCU_PIPES = {"128x3xg": {"fma_pipe_cycles_active": 0.625, "issue_slots_active": 0.656}}
 SAMPLE_RADII = (0, 9, 18, 27, 36, 45, 54, 63)   # oracle sample: ~1 s on 16 cores
 SAMPLE_MASS_INDEX = 2          # 0.1 eV
 
