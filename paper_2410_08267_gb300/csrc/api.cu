@@ -225,6 +225,11 @@ public:
         }
     }
     unsigned char* data() { return p_; }
+    static size_t capacity()
+    {
+        std::lock_guard<std::mutex> g(mu());
+        return buf().cap;
+    }
 
 private:
     struct Buf {
@@ -274,6 +279,13 @@ void verified_error(const double* mixed, const double* fp64, double* err, int n)
 }  // namespace
 
 namespace nuprof {
+
+size_t staging_capacity() { return Stage::capacity(); }
+int staging_reserve(size_t bytes)
+{
+    Stage st(bytes);
+    return Stage::capacity() >= bytes ? NU_OK : NU_ENOMEM;
+}
 
 const DevProblem& profile_desc(const nu_profile* h) { return h->hdp; }
 nu_profile* profile_twin(const nu_profile* h) { return h->twin; }
@@ -452,11 +464,11 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     const size_t o_mass = carve((size_t)nm * 3 * sizeof(double));   // scales, then norms
     const int nft = relic->f_kind == NU_F_TABLE ? relic->n_table : 0;
     const size_t o_ftab = carve((size_t)(nft > 0 ? nft : 1) * sizeof(double));   // tabulated f (FP64)
+    const size_t o_cnt = carve((size_t)n_radii * sizeof(unsigned));   // zero in the upload image
     const size_t upload_end = off;                         // everything above is uploaded
     // tile sums sized for the smallest tile shape, so that any batch shape fits
     const size_t tps_alloc = (size_t)(((long long)nq * nmu + kMinTile - 1) / kMinTile);
     const size_t o_part = carve((size_t)n_radii * tps_alloc * 2 * nm * sizeof(double));
-    const size_t o_cnt = carve((size_t)n_radii * sizeof(unsigned));
     const size_t o_out = carve((size_t)n_radii * nm * sizeof(double));
     const size_t o_err = carve((size_t)n_radii * nm * sizeof(double));
     const bool keep_qi = (o.flags & NU_FLAG_KEEP_QI) != 0;
@@ -540,8 +552,9 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
         }
 
         cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
+        // one copy and no kernel: a request can be created while a resident server
+        // launch holds every SM
         if (cudaMemcpyAsync(base, stage, upload_end, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemsetAsync(base + o_cnt, 0, (size_t)n_radii * sizeof(unsigned), s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {   // the staging buffer is reused after this
             cudaGetLastError();
             h->mem.release();

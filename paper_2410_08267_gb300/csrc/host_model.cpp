@@ -343,9 +343,9 @@ long long device_bytes(int precision, int n_steps, int n_radii, int n_q, int n_m
     b += align256((size_t)n_mu * sizeof(double));                // wmu
     b += align256((size_t)n_mass * 3 * sizeof(double));          // mass scales, normalisations
     b += align256((size_t)(n_ftab > 0 ? n_ftab : 1) * sizeof(double));   // tabulated f (FP64)
+    b += align256((size_t)n_radii * sizeof(unsigned));           // per-radius counters (zero)
     if (h2d_bytes) *h2d_bytes = (long long)b;                    // everything above is uploaded
     b += align256((size_t)n_radii * tiles_per_seg * 2 * n_mass * sizeof(double));
-    b += align256((size_t)n_radii * sizeof(unsigned));
     b += 2 * align256((size_t)n_radii * n_mass * sizeof(double));   // out, err
     if (keep_qi) b += align256((size_t)n_radii * n_q * n_mu * sz);
     return (long long)b;

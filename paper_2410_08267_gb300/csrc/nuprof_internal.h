@@ -127,6 +127,21 @@ struct DevProblem {
     volatile unsigned* done_flag;
 };
 
+// Work queue of a resident server launch (page-locked host memory that the
+// kernel reads through its device pointer).  The host appends requests to the
+// launch's descriptor and tile-prefix arrays while it runs and publishes them;
+// CTAs that claim a tile not yet published wait for it, each wait bounded.
+// `word` holds (state << 32) | published tiles and is changed only by
+// compare-and-swap, by the host (publish, close) and by a CTA whose wait ran
+// out (expire): so no tile is ever published after a CTA has given up on it.
+enum QueueState : unsigned { kQueueOpen = 0u, kQueueClosed = 1u, kQueueExpired = 2u };
+struct QueueCtl {
+    unsigned long long word;        // (state << 32) | published tiles
+    unsigned n_probs;               // descriptors published (written before `word`)
+    unsigned want_work;             // set by a CTA that found no published tile
+    unsigned long long wait_limit_ns;   // bound on one CTA's wait for a tile
+};
+
 // Accessors used by the request server (api.cu).
 const DevProblem& profile_desc(const nu_profile* h);
 int profile_n_radii(const nu_profile* h);
@@ -134,6 +149,11 @@ int profile_n_out(const nu_profile* h);   // n_mass * n_radii result values
 int profile_n_steps(const nu_profile* h);
 long long profile_n_traj(const nu_profile* h);
 int profile_read(const nu_profile* h, double* out, double* err, void* stream);
+// The page-locked staging buffer of create and result: its size, and growing
+// it (which may synchronize the device: not while a resident launch waits on
+// the host).
+size_t staging_capacity();
+int staging_reserve(size_t bytes);
 // NU_FLAG_VERIFY: the FP64 twin of a handle (nullptr without the flag), a
 // launch of the twin alone with an event after it, and a query of that event
 // (NU_OK done, NU_EAGAIN running, NU_EBUSY never run, NU_ECUDA).
@@ -144,7 +164,8 @@ int profile_twin_query(const nu_profile* h);
 // Kernel launch helpers (traj_kernel.cu).
 int launch_traj(int precision, int tpt, int block, int grid, size_t smem_bytes,
                 const DevProblem* d_probs, const int* d_tile_prefix, int n_probs, int n_tiles,
-                unsigned* d_tile_counter, void* stream, bool gtab = false);
+                unsigned* d_tile_counter, void* stream, bool gtab = false,
+                QueueCtl* d_queue = nullptr);
 int launch_traj_tally(int precision, int tpt, int block, int grid, size_t smem_bytes,
                       const DevProblem* d_probs, const int* d_tile_prefix, int n_probs, int n_tiles,
                       unsigned* d_tile_counter, unsigned long long* d_tallies, void* stream);

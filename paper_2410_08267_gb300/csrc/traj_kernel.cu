@@ -560,6 +560,58 @@ __device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const 
     y = ny;
 }
 
+// ---------------------------------------------------------------------------
+// Work queue of a resident launch (see QueueCtl).  Thread 0 of a CTA has
+// claimed tile g; it returns g once the host has published it, or -1 when the
+// launch ends: the queue was closed (or has expired) with g beyond its last
+// published tile, or this CTA's wait ran past the limit and it expired the
+// queue itself (by compare-and-swap on the same word the host publishes
+// through, so the tile it gave up on can never be published afterwards).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long load_acquire_sys(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned load_acquire_sys(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.sys.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ int queue_wait(QueueCtl* q, unsigned g, int* n_probs)
+{
+    const unsigned long long t0 = globaltimer_ns();
+    bool asked = false;
+    for (;;) {
+        const unsigned long long w = load_acquire_sys(&q->word);
+        const unsigned published = (unsigned)w;
+        if (g < published) {
+            *n_probs = (int)load_acquire_sys(&q->n_probs);
+            return (int)g;
+        }
+        if ((unsigned)(w >> 32) != kQueueOpen) return -1;
+        if (!asked) {
+            atomicExch_system(&q->want_work, 1u);
+            asked = true;
+        }
+        if (globaltimer_ns() - t0 > q->wait_limit_ns) {
+            const unsigned long long expired = ((unsigned long long)kQueueExpired << 32) | published;
+            if (atomicCAS_system(&q->word, w, expired) == w) return -1;
+            continue;                          // the host changed the word: look again
+        }
+        __nanosleep(1000);
+    }
+}
+
 // The packed path asks for two 512-thread CTAs per SM (at most 64 registers):
 // it issues few instructions per trajectory, so it needs many warps to hide
 // the latency of its dependent chains.
@@ -567,14 +619,18 @@ template <typename T, int TPT, bool COUNT, bool PACKED = false, bool GTAB = fals
 __global__ void __launch_bounds__(512, PACKED ? 2 : 1)
 traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_prefix,
             int n_probs, int n_tiles, unsigned* __restrict__ tile_counter,
-            unsigned long long* __restrict__ tallies)
+            unsigned long long* __restrict__ tallies, QueueCtl* queue)
 {
     using Ctr = typename std::conditional<COUNT, Tally, NoTally>::type;
     Ctr ctr;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s_coef = reinterpret_cast<T*>(smem_raw);
     __shared__ int s_tile;
+    __shared__ int s_req;
     __shared__ int s_last;
+    // the descriptor of the tile's request, read through L2 (requests published
+    // into a resident launch are never served from a stale L1 line)
+    __shared__ __align__(16) DevProblem s_prob;
     __shared__ double s_red[32][2];
 
     const int lane = threadIdx.x & 31;
@@ -583,18 +639,35 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
     int cur = -1;
 
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
+        if (threadIdx.x == 0) {
+            const unsigned claimed = atomicAdd(tile_counter, 1u);
+            int np = n_probs;
+            int t = queue ? queue_wait(queue, claimed, &np)
+                          : (claimed < (unsigned)n_tiles ? (int)claimed : -1);
+            // request that owns global tile t: last p with tile_prefix[p] <= t
+            if (t >= 0) {
+                int lo = 0, hi = np - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldcg(&tile_prefix[mid]) <= t) lo = mid; else hi = mid - 1;
+                }
+                s_req = lo;
+            }
+            s_tile = t;
+        }
         __syncthreads();
         const int g = s_tile;
-        if (g >= n_tiles) break;
-
-        // request that owns global tile g: last p with tile_prefix[p] <= g
-        int lo = 0, hi = n_probs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&tile_prefix[mid]) <= g) lo = mid; else hi = mid - 1;
+        if (g < 0) break;
+        const int lo = s_req;
+        {
+            constexpr int kWords = (int)(sizeof(DevProblem) / sizeof(unsigned));
+            static_assert(sizeof(DevProblem) % sizeof(unsigned) == 0, "descriptor words");
+            const unsigned* src = reinterpret_cast<const unsigned*>(probs + lo);
+            unsigned* dst = reinterpret_cast<unsigned*>(&s_prob);
+            for (int i = threadIdx.x; i < kWords; i += blockDim.x) dst[i] = __ldcg(&src[i]);
         }
-        const DevProblem& P = probs[lo];
+        __syncthreads();
+        const DevProblem& P = s_prob;
         const int n_steps = P.n_steps;
 
         // coefficient table: staged once per request into shared memory, or
@@ -610,7 +683,7 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
         }
 
         const int tps = P.tiles_per_seg;
-        const int lt = g - __ldg(&tile_prefix[lo]);
+        const int lt = g - __ldcg(&tile_prefix[lo]);
         const int seg = lt / tps;
         const int tis = lt - seg * tps;
         const int n_mu = P.n_mu;
@@ -875,7 +948,7 @@ size_t coef_smem_bytes(int precision, int n_steps, int tpt)
 template <typename T, int TPT, bool COUNT, bool PACKED = false, bool GTAB = false>
 static int launch_t(int block, int grid, size_t smem, const DevProblem* d_probs, const int* d_prefix,
                     int n_probs, int n_tiles, unsigned* d_counter, unsigned long long* d_tallies,
-                    cudaStream_t s)
+                    cudaStream_t s, QueueCtl* d_queue = nullptr)
 {
     auto k = traj_kernel<T, TPT, COUNT, PACKED, GTAB>;
     if (GTAB) smem = 0;
@@ -884,7 +957,7 @@ static int launch_t(int block, int grid, size_t smem, const DevProblem* d_probs,
             cudaSuccess)
             return NU_ECUDA;
     }
-    k<<<grid, block, smem, s>>>(d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies);
+    k<<<grid, block, smem, s>>>(d_probs, d_prefix, n_probs, n_tiles, d_counter, d_tallies, d_queue);
     if (cudaGetLastError() != cudaSuccess) return NU_ECUDA;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
@@ -895,25 +968,25 @@ static int launch_t(int block, int grid, size_t smem, const DevProblem* d_probs,
 template <bool GTAB>
 static int launch_shape(int precision, int tpt, int block, int grid, size_t smem,
                         const DevProblem* d_probs, const int* d_prefix, int n_probs, int n_tiles,
-                        unsigned* d_counter, cudaStream_t s)
+                        unsigned* d_counter, cudaStream_t s, QueueCtl* q)
 {
     if (precision == NU_FP64) {
-        if (tpt == 2) return launch_t<double, 2, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
-        return launch_t<double, 1, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+        if (tpt == 2) return launch_t<double, 2, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s, q);
+        return launch_t<double, 1, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s, q);
     }
-    if (tpt == 3) return launch_t<float, 2, false, true, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
-    if (tpt == 2) return launch_t<float, 2, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
-    return launch_t<float, 1, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s);
+    if (tpt == 3) return launch_t<float, 2, false, true, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s, q);
+    if (tpt == 2) return launch_t<float, 2, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s, q);
+    return launch_t<float, 1, false, false, GTAB>(block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, nullptr, s, q);
 }
 
 int launch_traj(int precision, int tpt, int block, int grid, size_t smem, const DevProblem* d_probs,
                 const int* d_prefix, int n_probs, int n_tiles, unsigned* d_counter, void* stream,
-                bool gtab)
+                bool gtab, QueueCtl* d_queue)
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (gtab || smem > kMaxStagedSmem)   // a table too large to stage is read through L1
-        return launch_shape<true>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
-    return launch_shape<false>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s);
+        return launch_shape<true>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s, d_queue);
+    return launch_shape<false>(precision, tpt, block, grid, smem, d_probs, d_prefix, n_probs, n_tiles, d_counter, s, d_queue);
 }
 
 template <bool GTAB>
