@@ -249,14 +249,17 @@ def paper_grid_once(nu, torch, stream, reps=10):
                                 "the C version 'a few seconds' per mass on a laptop CPU")}
 
 
-def serve_once(nu, rate, n_requests, seed=2412, batched=True, chunk=0, budget=8 << 30):
+def serve_once(nu, rate, n_requests, seed=2412, batched=True, chunk=0, budget=8 << 30,
+               resident=False, linger_ms=0.0):
     """The serving workload (Poisson arrivals, mixed requests) through the
     continuous-batching server, or through its one-request-per-launch form.
     chunk 0: whole runs, requests join at the next launch; chunk > 0: each
     launch advances every request by that many steps, so requests also join
-    ones already part-way through."""
+    ones already part-way through; resident: whole runs, and requests that
+    arrive while a launch runs join it through the device work queue."""
     reqs = W.serving_stream(rate=rate, n_requests=n_requests, seed=seed)
-    srv = (nu.nu_server_create(device_bytes=budget, chunk_steps=chunk, max_active=64) if batched
+    srv = (nu.nu_server_create(device_bytes=budget, chunk_steps=chunk, max_active=64,
+                               resident=resident, linger_ms=linger_ms) if batched
            else nu.nu_server_create(device_bytes=budget, chunk_steps=0, max_active=1))
     try:
         wall, lat, failed = drive_stream(nu, srv, reqs)
@@ -265,11 +268,13 @@ def serve_once(nu, rate, n_requests, seed=2412, batched=True, chunk=0, budget=8 
         nu.nu_server_destroy(srv)
     lat = np.asarray(lat)
     mode = ("one_per_launch" if not batched else
-            "continuous" if chunk == 0 else f"continuous_chunk{chunk}")
+            (f"resident_linger{linger_ms:g}" if resident else
+             "continuous" if chunk == 0 else f"continuous_chunk{chunk}"))
     return {"rate_per_s": rate, "requests": n_requests, "mode": mode,
             "profiles_per_s": len(lat) / wall, "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None, "failed": failed,
             "launches": st["iterations"], "max_active": st["max_active_seen"],
+            "joined_running_launch": st["joined"], "queue_expired": st["queue_expired"],
             "traj_steps_per_s": st["traj_steps"] / wall, "gpu_busy_frac": st["busy_ms"] / 1e3 / wall}
 
 
@@ -504,6 +509,7 @@ def bench_ours(args):
                 continue
             serving[key] = {"continuous": serve_once(nu, rate, n_req, batched=True),
                             "continuous_chunk100": serve_once(nu, rate, n_req, batched=True, chunk=100),
+                            "resident": serve_once(nu, rate, n_req, batched=True, resident=True),
                             "one_per_launch": serve_once(nu, rate, n_req, batched=False)}
 
     # ---- the two batch workloads (1024 uneven halos; 256 halos of new physics) ----
@@ -646,10 +652,14 @@ def bench_serve_sweep(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2410_08267_gb300 import nuprof as nu
-    for rate in (10, 30, 100, 300, 1000, 3000, 5000):
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    for rate in rates:
         n_req = int(min(args.serve_requests, max(20, rate * 2)))
-        for batched, chunk in ((True, 0), (True, 100), (False, 0)):
-            r = serve_once(nu, rate, n_req, batched=batched, chunk=chunk)
+        for batched, chunk, res, linger in ((True, 0, False, 0.0), (True, 100, False, 0.0),
+                                            (True, 0, True, 0.0), (True, 0, True, 2.0),
+                                            (False, 0, False, 0.0)):
+            r = serve_once(nu, rate, n_req, batched=batched, chunk=chunk, resident=res,
+                           linger_ms=linger)
             print(json.dumps({"metric": "served profiles/s", **r}), flush=True)
     return 0
 
@@ -675,6 +685,8 @@ def main():
                     help="fp64: the verification mode (FP64 state and force)")
     ap.add_argument("--main-only", action="store_true",
                     help="skip the serving and mass-reuse legs (profiler runs)")
+    ap.add_argument("--serve-rates", default="10,30,100,300,1000,3000,5000",
+                    help="request rates of --serve-sweep")
     ap.add_argument("--serve-sweep", action="store_true",
                     help="only the serving workload at rates 10..5000 /s, one JSON line per rate and mode")
     args = ap.parse_args()

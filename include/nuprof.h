@@ -377,6 +377,15 @@ typedef struct nu_server_opts {
     double step_budget;      /* trajectory-steps per launch (<= 0 -> 4e9): with many
                                 requests active the chunk shrinks to fit it, which
                                 bounds each launch's duration                      */
+    int resident;            /* 1: requests that arrive while a launch runs join it
+                                through a device work queue instead of waiting for
+                                the next launch (whole runs: chunk_steps must be 0;
+                                needs host-native atomics, else NU_ENOTSUP)        */
+    double linger_ms;        /* resident: how long the queue stays open after it
+                                runs dry, for arrivals to join (0: close at once)  */
+    double queue_wait_ms;    /* resident: bound on one CTA's wait for queued work
+                                (<= 0 -> 1000); when it runs out the launch ends
+                                and the server counts it in queue_expired         */
 } nu_server_opts;
 
 typedef struct nu_serve_stats {
@@ -389,6 +398,8 @@ typedef struct nu_serve_stats {
     int status;              /* NU_OK, or the error that stopped the server        */
     long long arena_bytes, arena_peak;
     long long early;         /* results delivered while their last launch still ran */
+    long long joined;        /* resident: requests admitted into a running launch    */
+    long long queue_expired; /* resident: launches ended by a CTA's bounded queue wait */
 } nu_serve_stats;
 
 /* Start a server on the current device.  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */

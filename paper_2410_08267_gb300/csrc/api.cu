@@ -283,7 +283,7 @@ namespace nuprof {
 size_t staging_capacity() { return Stage::capacity(); }
 int staging_reserve(size_t bytes)
 {
-    Stage st(bytes);
+    { Stage st(bytes); }   // grows the buffer; its lock is released before the size is read
     return Stage::capacity() >= bytes ? NU_OK : NU_ENOMEM;
 }
 

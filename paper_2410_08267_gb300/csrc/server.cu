@@ -207,6 +207,14 @@ struct nu_server {
     unsigned* h_flags = nullptr;            // page-locked, mapped: one per active slot
     unsigned* d_flags = nullptr;            // the same memory as the device sees it
     unsigned* d_counts = nullptr;           // radii finished, per active slot (arena)
+
+    // resident launches: the work queue (page-locked, mapped) through which
+    // requests admitted during a launch join it
+    QueueCtl* h_q = nullptr;
+    QueueCtl* d_q = nullptr;
+    bool resident_running = false;          // a resident launch is waiting on the host
+    bool defer_close = false;               // a request can only be admitted after it ends
+    long long joined = 0, queue_expired = 0;   // statistics (under mu)
 };
 
 void nu_server::finish(Active& a, int rc, std::vector<double>* out, std::vector<double>* err)
@@ -267,6 +275,13 @@ bool nu_server::admit_one()
     const size_t state_bytes = (size_t)info.n_traj * 4 * sz;
     if (rc == NU_OK && up256((size_t)info.device_bytes) + up256(state_bytes) > capacity)
         rc = NU_ENOMEM;                       // can never fit: refuse
+    // while a resident launch waits on this thread, nothing may synchronize the
+    // device: a request whose upload would grow the page-locked staging buffer
+    // waits for the launch to end
+    if (rc == NU_OK && resident_running && (size_t)info.h2d_bytes > staging_capacity()) {
+        defer_close = true;
+        return false;
+    }
     nu_profile* h = nullptr;
     void* state = nullptr;
     if (rc == NU_OK) {
@@ -276,7 +291,10 @@ bool nu_server::admit_one()
         if (!state || rc == NU_ENOMEM) {
             arena.release(state);
             if (h) nu_profile_destroy(h);
-            if (!active.empty() || !staged.empty()) return false;   // wait for room
+            if (!active.empty() || !staged.empty()) {                // wait for room
+                defer_close = resident_running;
+                return false;
+            }
             rc = NU_ENOMEM;                   // nothing to wait for: refuse
             state = nullptr;
             h = nullptr;
@@ -418,16 +436,99 @@ void nu_server::run()
             (h_flags && cudaMemsetAsync(d_counts, 0, n * sizeof(unsigned), compute) != cudaSuccess))
             rc = NU_ECUDA;
         int grid = 0, per_sm = 0, sms = 0;
+        // a resident launch stages tables up to the largest a request may have
+        // (requests join it later), so that its shared memory fits any of them
+        const bool res = o.resident != 0;
+        if (res) smem = std::max(smem, coef_smem_bytes(o.precision, NU_MAX_STEPS, tpt));
         if (rc == NU_OK) rc = max_ctas_per_sm(o.precision, tpt, o.block, smem, &per_sm, gtab);
         if (rc == NU_OK && (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
                             per_sm < 1))
             rc = NU_ECUDA;
+        if (rc == NU_OK && res) {                // open the queue with this launch's requests
+            h_q->n_probs = (unsigned)n;
+            h_q->want_work = 0u;
+            h_q->wait_limit_ns = (unsigned long long)(o.queue_wait_ms * 1e6);
+            __atomic_store_n(&h_q->word, ((unsigned long long)kQueueOpen << 32) | (unsigned)prefix[n],
+                             __ATOMIC_SEQ_CST);
+        }
         if (rc == NU_OK) {
-            grid = std::max(1, std::min(prefix[n], per_sm * sms));
+            // a resident launch keeps every CTA: the ones without work wait for
+            // requests that join
+            grid = res ? per_sm * sms : std::max(1, std::min(prefix[n], per_sm * sms));
             rc = launch_traj(o.precision, tpt, o.block, grid, smem, d_desc[slot], d_prefix[slot], n,
-                             prefix[n], d_ctrl, compute, gtab);
+                             prefix[n], d_ctrl, compute, gtab, res ? d_q : nullptr);
         }
         const auto t_launch = Clock::now();
+        auto t_publish = t_launch;               // resident: the last time work joined
+        auto t_want = t_launch;                  // resident: when the queue was first seen dry
+        bool queue_open = res && rc == NU_OK;
+        bool want_seen = false;
+        resident_running = queue_open;
+        defer_close = false;
+        // resident: no more joins; CTAs that run dry then leave the launch
+        auto close_queue = [&]() {
+            unsigned long long w = __atomic_load_n(&h_q->word, __ATOMIC_SEQ_CST);
+            while ((unsigned)(w >> 32) == kQueueOpen) {
+                const unsigned long long closed = ((unsigned long long)kQueueClosed << 32) | (unsigned)w;
+                if (__atomic_compare_exchange_n(&h_q->word, &w, closed, false, __ATOMIC_SEQ_CST,
+                                                __ATOMIC_SEQ_CST))
+                    break;
+            }
+            queue_open = false;
+        };
+        // resident: append staged requests to the running launch and publish them
+        auto join_staged = [&]() {
+            static const unsigned zero = 0u;
+            size_t k = 0;
+            for (; k < staged.size() && active.size() < (size_t)o.max_active; ++k) {
+                Active& a = staged[k];
+                const int i = (int)active.size();
+                DevProblem d = profile_desc(a.h);
+                const long long seg = (long long)d.n_q * d.n_mu;
+                d.tile = tile;
+                d.tiles_per_seg = (int)((seg + tile - 1) / tile);
+                d.state = a.state;
+                d.step_begin = 0;
+                d.step_end = a.n_steps;
+                d.done_count = nullptr;
+                d.done_flag = nullptr;
+                const bool signal = !profile_twin(a.h);
+                if (signal) {
+                    h_flags[i] = 0u;
+                    d.done_count = d_counts + i;
+                    d.done_flag = d_flags + i;
+                }
+                const int next = prefix.back() + d.tiles_per_seg * d.n_radii;
+                if (cudaMemcpyAsync(d_desc[slot] + i, &d, sizeof(DevProblem), cudaMemcpyHostToDevice,
+                                    upload) != cudaSuccess ||
+                    cudaMemcpyAsync(d_prefix[slot] + i + 1, &next, sizeof(int), cudaMemcpyHostToDevice,
+                                    upload) != cudaSuccess ||
+                    cudaMemcpyAsync(d_counts + i, &zero, sizeof(unsigned), cudaMemcpyHostToDevice,
+                                    upload) != cudaSuccess ||
+                    cudaStreamSynchronize(upload) != cudaSuccess) {
+                    cudaGetLastError();
+                    break;                       // it stays staged for the next launch
+                }
+                __atomic_store_n(&h_q->n_probs, (unsigned)(i + 1), __ATOMIC_SEQ_CST);
+                unsigned long long expect = ((unsigned long long)kQueueOpen << 32) | (unsigned)prefix.back();
+                const unsigned long long want = ((unsigned long long)kQueueOpen << 32) | (unsigned)next;
+                if (!__atomic_compare_exchange_n(&h_q->word, &expect, want, false, __ATOMIC_SEQ_CST,
+                                                 __ATOMIC_SEQ_CST)) {
+                    queue_open = false;          // closed or expired meanwhile: next launch
+                    break;
+                }
+                active.push_back(a);
+                desc.push_back(d);
+                prefix.push_back(next);
+                early_st.push_back(signal ? 1 : 0);
+                steps_this += profile_n_traj(a.h) * a.n_steps;
+                t_publish = Clock::now();
+                std::lock_guard<std::mutex> g(mu);
+                ++joined;
+                max_active_seen = std::max(max_active_seen, (int)active.size());
+            }
+            staged.erase(staged.begin(), staged.begin() + k);
+        };
         if (rc == NU_OK && cudaEventRecord(ev, compute) != cudaSuccess) rc = NU_ECUDA;
         // bounded wait for the launch; requests that arrive meanwhile are
         // admitted now (their tables upload on a separate stream) and join
@@ -439,12 +540,12 @@ void nu_server::run()
                 rc = NU_ECUDA;
                 break;
             }
-            if (ms_since(t_launch) > o.gpu_timeout_ms) {
+            if (ms_since(t_publish) > o.gpu_timeout_ms) {
                 rc = NU_ETIMEDOUT;
                 break;
             }
             // deliver requests that have finished inside the running launch
-            for (int i = 0; i < n; ++i) {
+            for (size_t i = 0; i < active.size(); ++i) {
                 if (early_st[i] != 1 || reinterpret_cast<volatile unsigned*>(h_flags)[i] != 1u) continue;
                 const int nr = profile_n_out(active[i].h);
                 std::vector<double> out(nr), err(nr);
@@ -455,12 +556,42 @@ void nu_server::run()
                 ++early;
             }
             deliver_verified();
+            const bool admitted_one = admit_one();
+            if (queue_open) {
+                if (!staged.empty()) join_staged();
+                // close the queue (no more joins; the launch ends when its CTAs
+                // have run dry) when it has run dry with nothing queued for
+                // linger_ms, when its slots are used up while requests wait,
+                // when a request can only be admitted after the launch, or
+                // when the launch has lived a quarter of the GPU time limit
+                if (!want_seen && __atomic_load_n(&h_q->want_work, __ATOMIC_ACQUIRE) != 0u) {
+                    want_seen = true;
+                    t_want = Clock::now();
+                }
+                bool waiting;
+                {
+                    std::lock_guard<std::mutex> g(mu);
+                    waiting = !pending.empty();
+                }
+                const auto t_dry = std::max(t_want, t_publish);
+                bool close = defer_close || ms_since(t_launch) > 0.25 * o.gpu_timeout_ms ||
+                             (active.size() >= (size_t)o.max_active && (waiting || !staged.empty()));
+                if (want_seen && !waiting && staged.empty() && ms_since(t_dry) >= o.linger_ms) close = true;
+                if (close) close_queue();
+            }
             // poll closely at first (short launches finish within a few ms and a
             // sleep would add its granularity to every chunk), then back off
-            if (!admit_one()) {
+            if (!admitted_one) {
                 if (ms_since(t_launch) < 2.0) std::this_thread::yield();
                 else std::this_thread::sleep_for(std::chrono::microseconds(50));
             }
+        }
+        if (queue_open) close_queue();           // an error ended the wait: no CTA waits on
+        resident_running = false;
+        if (res && rc == NU_OK &&
+            (unsigned)(__atomic_load_n(&h_q->word, __ATOMIC_SEQ_CST) >> 32) == kQueueExpired) {
+            std::lock_guard<std::mutex> g(mu);
+            ++queue_expired;                     // a CTA's bounded wait ended the launch
         }
         const double launch_ms = ms_since(t_launch);
         slot ^= 1;
@@ -549,6 +680,9 @@ int nu_server_create(const nu_server_opts* opts, nu_server** out)
     if (o.tpt == kTptPacked && o.precision != NU_MIXED) return NU_EINVAL;
     if (o.chunk_steps < 0) return NU_EINVAL;
     if (o.gpu_timeout_ms <= 0.0) o.gpu_timeout_ms = 60000.0;
+    if (o.resident && o.chunk_steps != 0) return NU_EINVAL;   // resident launches run whole requests
+    if (o.linger_ms < 0.0) return NU_EINVAL;
+    if (o.queue_wait_ms <= 0.0) o.queue_wait_ms = 1000.0;
     if (o.step_budget <= 0.0) o.step_budget = 4e9;
     if (o.device_bytes < ((size_t)1 << 20)) return NU_EINVAL;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
@@ -595,12 +729,35 @@ int nu_server_create(const nu_server_opts* opts, nu_server** out)
         s->h_flags = nullptr;
         s->d_flags = nullptr;
     }
+    if (o.resident) {
+        // the queue word is changed by compare-and-swap from the host and the GPU
+        int native = 0;
+        if (!s->h_flags ||
+            cudaDeviceGetAttribute(&native, cudaDevAttrHostNativeAtomicSupported, s->device) != cudaSuccess ||
+            !native) {
+            cudaGetLastError();
+            if (s->h_flags) cudaFreeHost(s->h_flags);
+            return fail(NU_ENOTSUP);
+        }
+        if (cudaHostAlloc(reinterpret_cast<void**>(&s->h_q), sizeof(QueueCtl), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_q), s->h_q, 0) != cudaSuccess) {
+            cudaGetLastError();
+            if (s->h_q) cudaFreeHost(s->h_q);
+            cudaFreeHost(s->h_flags);
+            return fail(NU_ECUDA);
+        }
+        std::memset(s->h_q, 0, sizeof(QueueCtl));
+        // room for typical uploads, so that admissions during a launch never
+        // have to grow the staging buffer
+        staging_reserve((size_t)16 << 20);
+    }
     if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->verify, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (s->h_flags) cudaFreeHost(s->h_flags);
+        if (s->h_q) cudaFreeHost(s->h_q);
         return fail(NU_ECUDA);
     }
     nu_server* raw = s.get();
@@ -711,6 +868,8 @@ int nu_server_stats(nu_server* s, nu_serve_stats* out)
     out->arena_peak = (long long)s->arena.peak();
     out->status = s->fatal;
     out->early = s->early;
+    out->joined = s->joined;
+    out->queue_expired = s->queue_expired;
     if (!s->latencies.empty()) {
         std::vector<double> l = s->latencies;
         std::sort(l.begin(), l.end());
@@ -753,6 +912,7 @@ void nu_server_destroy(nu_server* s)
     // they are leaked rather than freed under a running kernel
     if (gpu_ok) {
         if (s->h_flags) cudaFreeHost(s->h_flags);
+        if (s->h_q) cudaFreeHost(s->h_q);
         if (s->o.alloc) {
             if (s->o.free) s->o.free(s->block, s->o.device_bytes, s->o.alloc_ctx);
         } else {

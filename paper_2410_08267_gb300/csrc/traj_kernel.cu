@@ -608,7 +608,7 @@ __device__ int queue_wait(QueueCtl* q, unsigned g, int* n_probs)
             if (atomicCAS_system(&q->word, w, expired) == w) return -1;
             continue;                          // the host changed the word: look again
         }
-        __nanosleep(1000);
+        __nanosleep(2000);
     }
 }
 

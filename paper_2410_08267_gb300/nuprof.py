@@ -82,7 +82,8 @@ class nu_server_opts(C.Structure):
     _fields_ = [("device_bytes", C.c_size_t), ("max_active", C.c_int), ("chunk_steps", C.c_int),
                 ("precision", C.c_int), ("block", C.c_int), ("tpt", C.c_int), ("flags", C.c_int),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("gpu_timeout_ms", C.c_double), ("step_budget", C.c_double)]
+                ("gpu_timeout_ms", C.c_double), ("step_budget", C.c_double),
+                ("resident", C.c_int), ("linger_ms", C.c_double), ("queue_wait_ms", C.c_double)]
 
 
 class nu_serve_stats(C.Structure):
@@ -92,7 +93,8 @@ class nu_serve_stats(C.Structure):
                 ("traj_steps", C.c_longlong), ("busy_ms", C.c_double), ("p50_ms", C.c_double),
                 ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("pending", C.c_int),
                 ("active", C.c_int), ("max_active_seen", C.c_int), ("status", C.c_int),
-                ("arena_bytes", C.c_longlong), ("arena_peak", C.c_longlong), ("early", C.c_longlong)]
+                ("arena_bytes", C.c_longlong), ("arena_peak", C.c_longlong), ("early", C.c_longlong),
+                ("joined", C.c_longlong), ("queue_expired", C.c_longlong)]
 
 
 class nu_peaks(C.Structure):
@@ -263,9 +265,11 @@ nu_strerror = strerror
 def nu_server_create(device_bytes: int, precision: int = NU_MIXED, max_active: int = 0,
                      chunk_steps: int = 100, block: int = 0, tpt: int = 0, flags: int = 0,
                      gpu_timeout_ms: float = 0.0, torch_alloc: bool = False,
-                     step_budget: float = 0.0) -> C.c_void_p:
+                     step_budget: float = 0.0, resident: bool = False, linger_ms: float = 0.0,
+                     queue_wait_ms: float = 0.0) -> C.c_void_p:
     o = nu_server_opts()
     o.step_budget = step_budget
+    o.resident, o.linger_ms, o.queue_wait_ms = int(bool(resident)), linger_ms, queue_wait_ms
     o.device_bytes, o.max_active, o.chunk_steps, o.precision = device_bytes, max_active, chunk_steps, precision
     o.block, o.tpt, o.flags, o.gpu_timeout_ms = block, tpt, flags, gpu_timeout_ms
     if torch_alloc:

@@ -179,3 +179,11 @@ def test_verify_rules():
     with pytest.raises(nu.NuError) as e:
         nu.plan(pb.replace(precision=W.FP64), flags=nu.NU_FLAG_VERIFY)
     assert e.value.code == nu.NU_EINVAL
+
+
+def test_resident_server_needs_whole_runs():
+    """A resident server runs whole requests: chunked launches are refused
+    before any GPU work."""
+    with pytest.raises(nu.NuError) as e:
+        nu.nu_server_create(device_bytes=64 << 20, chunk_steps=100, resident=True)
+    assert e.value.code == nu.NU_EINVAL

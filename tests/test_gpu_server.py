@@ -228,3 +228,60 @@ def test_served_profiles_match_the_oracle():
             assert_parity(out, pb, sel=sel, where="served")
     finally:
         nu.nu_server_destroy(srv)
+
+
+def _long_request(n_steps=2000):
+    """One request that keeps a launch busy for tens of milliseconds."""
+    M = 1e13
+    return W.Problem(M_h=M, c=W.c_of_M(M), xi_kind=W.XI_LINEAR, m_eV=0.1,
+                     radii=np.geomspace(1.0, 1000.0, 96), n_q=256, n_mu=64, n_steps=n_steps,
+                     z_end=4.0, precision=W.MIXED)
+
+
+def test_resident_launch_admits_requests_that_arrive_while_it_runs():
+    """Resident mode: requests submitted while a long request runs join that
+    launch through the device work queue instead of waiting for it to end,
+    and every result is bitwise the one the request gets alone."""
+    big = _long_request()
+    small = _stream(6, seed=57, max_radii=16, n_steps=400)
+    alone = [_alone(pb) for pb in [big] + small]
+    srv = nu.nu_server_create(device_bytes=1 << 30, chunk_steps=0, resident=True)
+    try:
+        tickets = [nu.nu_server_submit(srv, big)]
+        time.sleep(0.005)                      # the long request is on the GPU by now
+        tickets += [nu.nu_server_submit(srv, pb) for pb in small]
+        for t, pb, (a, ae) in zip(tickets, [big] + small, alone):
+            rc, out, err, _ = _wait(srv, t, pb.n_radii)
+            assert rc == nu.NU_OK
+            assert np.array_equal(out, a) and np.array_equal(err, ae)
+        st = nu.nu_server_stats(srv)
+        print("[server] resident:", {k: st[k] for k in ("iterations", "joined", "early", "queue_expired")})
+        assert st["joined"] >= 1, st
+        assert st["queue_expired"] == 0, st
+    finally:
+        nu.nu_server_destroy(srv)
+
+
+def test_resident_queue_wait_runs_out_and_ends_the_launch():
+    """The device-side wait for queued work is bounded: with the host keeping
+    the queue open (a long linger) and nothing arriving, every waiting CTA
+    gives up after queue_wait_ms, expires the queue and leaves, so the launch
+    ends by itself.  Its request is still complete and correct, and the server
+    goes on serving."""
+    pb = _stream(1, seed=58, max_radii=12, n_steps=200)[0]
+    ref = _alone(pb)
+    srv = nu.nu_server_create(device_bytes=256 << 20, chunk_steps=0, resident=True,
+                              linger_ms=60000.0, queue_wait_ms=20.0)
+    try:
+        t0 = time.time()
+        rc, out, err, _ = _wait(srv, nu.nu_server_submit(srv, pb), pb.n_radii)
+        assert rc == nu.NU_OK and np.array_equal(out, ref[0])
+        while nu.nu_server_stats(srv)["queue_expired"] < 1 and time.time() - t0 < 10.0:
+            time.sleep(0.005)
+        st = nu.nu_server_stats(srv)
+        assert st["queue_expired"] == 1 and st["status"] == nu.NU_OK, st
+        pb2 = _stream(2, seed=59, max_radii=8, n_steps=200)[1]
+        rc, out, _, _ = _wait(srv, nu.nu_server_submit(srv, pb2), pb2.n_radii)
+        assert rc == nu.NU_OK and np.array_equal(out, _alone(pb2)[0])
+    finally:
+        nu.nu_server_destroy(srv)
