@@ -213,11 +213,55 @@ void coef_table_into(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& 
     }
 }
 
+// Requests of a scan often share their halo, background and step grid (a
+// list of relic masses, a momentum-grid study): the last few tables are kept,
+// keyed by every input the table depends on.
+namespace {
+struct TableKey {
+    double v[14];
+    int k[3];
+    bool operator==(const TableKey& o) const
+    {
+        return std::memcmp(v, o.v, sizeof(v)) == 0 && std::memcmp(k, o.k, sizeof(k)) == 0;
+    }
+};
+TableKey table_key(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps)
+{
+    TableKey key;
+    std::memset(&key, 0, sizeof(key));
+    const double v[14] = {cosmo.Om, cosmo.h, halo.M_h, halo.c, halo.z0, halo.xi_p[0],
+                          halo.xi_p[1], halo.xi_p[2], halo.kappa_p[0], halo.kappa_p[1],
+                          halo.kappa_p[2], d.z_end, 0.0, 0.0};
+    std::memcpy(key.v, v, sizeof(v));
+    key.k[0] = halo.xi_kind;
+    key.k[1] = halo.kappa_kind;
+    key.k[2] = n_steps;
+    return key;
+}
+}  // namespace
+
 void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps,
                 std::vector<double>& tab)
 {
+    constexpr size_t kKept = 8;
+    static std::mutex mu;
+    static std::vector<std::pair<TableKey, std::vector<double>>> kept;   // most recent last
+    const TableKey key = table_key(cosmo, halo, d, n_steps);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        for (size_t i = 0; i < kept.size(); ++i) {
+            if (kept[i].first == key) {
+                tab = kept[i].second;
+                std::rotate(kept.begin() + i, kept.begin() + i + 1, kept.end());
+                return;
+            }
+        }
+    }
     tab.assign((size_t)n_steps * C_COUNT, 0.0);
     coef_table_into(cosmo, halo, d, n_steps, tab.data());
+    std::lock_guard<std::mutex> g(mu);
+    if (kept.size() == kKept) kept.erase(kept.begin());
+    kept.emplace_back(key, tab);
 }
 
 // |P| nodes: log-spaced on [q_min, q_max]; the integral of P^2 f dP is taken
