@@ -42,7 +42,8 @@ class OrParams(C.Structure):
 class OrDerived(C.Structure):
     _fields_ = [("H0", C.c_double), ("rho_bar0", C.c_double), ("R", C.c_double),
                 ("z_i", C.c_double), ("r200", C.c_double), ("r_s", C.c_double),
-                ("Ic", C.c_double), ("xi_zs", C.c_double), ("xi_ze", C.c_double)]
+                ("Ic", C.c_double), ("xi_zs", C.c_double), ("xi_ze", C.c_double),
+                ("force_scale", C.c_double)]
 
 
 def lib():
@@ -230,13 +231,14 @@ def profile(pb, radius_sel=None, n_threads: int = 0, return_qi: bool = False):
 
 def profile_perturbed(pb, eps: float, seed: int, radius_sel=None, n_threads: int = 0,
                       return_qi: bool = False, round_state: bool = False,
-                      step_noise: bool = False):
+                      step_noise: bool = False, force_noise: bool = False):
     """Conditioning probe: n/nbar with each trajectory's start velocity scaled by
     (1 + eps u), u ~ U[-1, 1) independent per trajectory (counter-based, seeded);
     with round_state the state is rounded to float32 after every RK4 step, with
     step_noise every state component is scaled by its own (1 + eps u) after
-    every step.  Not part of the method; eps = 0 without the options equals
-    profile() exactly."""
+    every step, with force_noise every force evaluation is scaled by 1 + eps
+    (odd seeds) or 1 - eps (even seeds).  Not part of the method; eps = 0
+    without the options equals profile() exactly."""
     p = params(pb)
     radii = np.ascontiguousarray(np.asarray(pb.radii, dtype=np.float64))
     n_r = len(radii)
@@ -251,7 +253,8 @@ def profile_perturbed(pb, eps: float, seed: int, radius_sel=None, n_threads: int
                                     n_sel, int(pb.n_q), float(pb.q_min), float(pb.q_max),
                                     int(pb.n_mu), int(pb.n_steps), float(pb.z_end), int(n_threads),
                                     float(eps), int(seed),
-                                    int(bool(round_state)) | (2 if step_noise else 0), _dptr(out),
+                                    int(bool(round_state)) | (2 if step_noise else 0)
+                                    | (4 if force_noise else 0), _dptr(out),
                                     _dptr(qi) if qi is not None else None)
     if rc != 0:
         raise ValueError(f"oracle rejected the problem (rc={rc})")

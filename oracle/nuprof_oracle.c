@@ -90,6 +90,7 @@ typedef struct {
     double r_s;         /* NFW scale radius, kpc                            */
     double Ic;          /* I(c) = ln(1+c) - c/(1+c)                          */
     double xi_zs, xi_ze;/* linear-growth window actually used               */
+    double force_scale; /* 1; the conditioning probe only: 1 + eps or 1 - eps */
 } or_derived;
 
 /* ---- Sec. II.B: halo parameters derived from (M_h, c, z0) --------------- */
@@ -109,6 +110,7 @@ int or_derive(const or_params* p, or_derived* d)
     d->Ic = log1p(p->c) - p->c / (1.0 + p->c);
     d->xi_zs = (p->xi_p[1] > 0.0) ? p->xi_p[1] : d->z_i;
     d->xi_ze = (p->xi_p[2] > 0.0) ? p->xi_p[2] : p->z0;
+    d->force_scale = 1.0;
     return 0;
 }
 
@@ -191,7 +193,7 @@ double or_dphidr(const or_params* p, const or_derived* d, double r, double z)
         Mhat = or_I(r / (d->r_s * zp1)) / d->Ic - rR3;
     else
         Mhat = 1.0 - rR3;
-    return OR_G_KPC * or_kappa(p, z) * zp1 * xi * p->M_h * Mhat / (r * r);
+    return OR_G_KPC * or_kappa(p, z) * zp1 * xi * p->M_h * Mhat / (r * r) * d->force_scale;
 }
 
 /* ---- Eq. eoms rewritten in u = ln a (dz/du = -(1+z), reading R2):
@@ -392,7 +394,11 @@ int or_profile(const or_params* p, const double* radii, int n_radii, int radii_u
  * FP64 computation) and bit 1, after every step, scales each component's
  * increment by (1 + eps u) and moves the component by eps u |x| or eps u |v|
  * (rounding-size noise at each step, as two FP64 codes with different
- * operation orders see it).  The spread of n/nbar over a
+ * operation orders see it); bit 2 multiplies every force evaluation by
+ * 1 + eps (odd seeds) or 1 - eps (even seeds), the systematic relative error
+ * that evaluating the force in a given precision leaves (an FP32 force
+ * carries a few 1e-7 in every evaluation, which rounding-size noise on the
+ * state does not represent).  The spread of n/nbar over a
  * few seeds measures how strongly the discrete RK4 map amplifies rounding-size
  * differences; eps = 0 and round_state = 0 reproduce or_profile bit for bit. */
 int or_profile_perturbed(const or_params* p, const double* radii, int n_radii, int radii_unit,
@@ -417,6 +423,8 @@ static int profile_impl(const or_params* p, const double* radii, int n_radii, in
 {
     or_derived d;
     if (or_derive(p, &d) != 0) return -1;
+    if (round_state & 4)                      /* probe: one relative force error per run */
+        d.force_scale = (seed & 1ULL) ? 1.0 + eps : 1.0 - eps;
     if (z_end <= 0.0) z_end = d.z_i;          /* default end: the paper's z_i (R7) */
     if (n_radii < 1 || n_mu < 1 || nsteps < 1 || !(z_end > p->z0) || !(p->m_eV > 0.0))
         return -1;
@@ -461,7 +469,7 @@ static int profile_impl(const or_params* p, const double* radii, int n_radii, in
                 for (int c = 0; c < 4; ++c)
                     s[c] += eps * (c < 2 ? xn : vn) * or_unit_noise(seed * 8 + (unsigned long long)c, ir, t);
             }
-            if (!round_state) {
+            if (!(round_state & 3)) {      /* no per-step rounding or noise */
                 or_integrate(p, &d, s, 0.0, u_end, nsteps);
             } else {
                 double du = u_end / (double)nsteps;

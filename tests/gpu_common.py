@@ -11,8 +11,11 @@ trajectory's state is perturbed by rounding-size noise at every step.  The
 probe measures this `spread`: the largest pairwise relative difference among
 the oracle and five seeded runs of it with noise of relative size EPS (a few
 ulps of the mode's precision) on the start state and on every step's
-increments; for the mixed mode the probe also rounds the state to float32
-after every step, which is what FP32 state storage does to the computation.
+increments, and with every force evaluation off by the relative error EPS
+(+EPS on odd seeds, -EPS on even ones: a force evaluated in the mode's
+precision carries such an error systematically, in every evaluation); for the
+mixed mode the probe also rounds the state to float32 after every step, which
+is what FP32 state storage does to the computation.
 
 A radius may miss TOL only where the oracle itself is not reproducible to
 that level under the mode's rounding (K x spread > TOL).  Such a radius is a
@@ -71,7 +74,8 @@ def oracle_with_spread(pb, sel=None, seeds=SEEDS):
     o = oracle.profile(pb.replace(precision=W.FP64), radius_sel=sel)
     eps = EPS[pb.precision]
     runs = [o] + [oracle.profile_perturbed(pb, eps, s, radius_sel=sel, step_noise=True,
-                                           round_state=(pb.precision == W.MIXED)) for s in seeds]
+                                           force_noise=True, round_state=(pb.precision == W.MIXED))
+                  for s in seeds]
     spread = np.zeros_like(o)
     for a, b in itertools.combinations(runs, 2):
         spread = np.maximum(spread, np.abs(a - b) / np.where(o != 0, np.abs(o), 1.0))

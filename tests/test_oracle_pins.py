@@ -447,3 +447,27 @@ def test_dense_table_of_fermi_dirac_reproduces_the_closed_form():
     assert np.allclose(a, b, rtol=2e-5, atol=0)
     m0 = base.replace(M_h=0.0, f_kind=W.F_TABLE, f_p=(1e-4, 60.0), f_table=tab)
     assert np.allclose(oracle.profile(m0), 1.0, rtol=1e-13)
+
+
+def test_conditioning_probe_force_error_is_a_relative_force_scale():
+    """The probe's systematic force error (not part of the method) is a
+    relative scale of every force evaluation: with eps = 0 it reproduces the
+    oracle bit for bit, and with a constant coupling kappa (Sec. IV.B, which
+    multiplies G in every evaluation) a force error of +eps (odd seed) or
+    -eps (even seed) equals the run with kappa scaled by 1 +/- eps and the
+    same seeded start-state noise, to rounding, at radii where the map is
+    well conditioned."""
+    pb = W.plain_small(precision=W.FP64)[0].replace(n_q=24, n_mu=8, n_steps=100,
+                                                    kappa_kind=W.KAPPA_CONST,
+                                                    kappa_p=(1.0, 0.0, 0.0))
+    sel = [9]                       # 300 kpc: regular orbits, amplification ~1e3
+    base = oracle.profile(pb, radius_sel=sel)[sel]
+    same = oracle.profile_perturbed(pb, 0.0, 1, radius_sel=sel, force_noise=True)[sel]
+    assert np.array_equal(same, base)
+    eps = 1e-3
+    for seed, k in ((1, 1.0 + eps), (2, 1.0 - eps)):
+        got = oracle.profile_perturbed(pb, eps, seed, radius_sel=sel, force_noise=True)[sel]
+        ref = oracle.profile_perturbed(pb.replace(kappa_p=(k, 0.0, 0.0)), eps, seed,
+                                       radius_sel=sel)[sel]
+        assert np.all(np.abs(got - ref) <= 1e-10 * np.abs(ref)), (seed, got, ref)
+        assert np.all(np.abs(got - base) > 1e-7 * np.abs(base))      # it does move
