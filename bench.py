@@ -340,11 +340,13 @@ def batch_leg(nu, torch, stream, problems, block, tpt, tflags, steps, flush, sam
             e = 0.0 if got[i][r] == ref[r] else abs(got[i][r] - ref[r]) / abs(ref[r])
             errs.append(e)
             if e > tol:
-                # the oracle's own spread at this radius under FP32 state rounding
-                # and rounding-size step noise (two seeds): where it reaches the
+                # the oracle's own spread at this radius under FP32 state rounding,
+                # rounding-size step noise and a relative force error of the same
+                # size (two seeds, one of each sign): where it reaches the
                 # tolerance the radius is chaotic under the mode's rounding
                 spr = max(abs(oracle.profile_perturbed(pb, 2.0 ** -22, seed, radius_sel=[r],
-                                                       step_noise=True, round_state=True)[r]
+                                                       step_noise=True, force_noise=True,
+                                                       round_state=True)[r]
                               - ref[r]) / abs(ref[r]) for seed in (1, 2))
                 misses.append({"request": i, "radius": r, "rel_err": e, "oracle_spread": spr})
     return {"kernel_ms_per_step": kms, "traj_steps_per_step": nominal,
@@ -593,6 +595,7 @@ def bench_ours(args):
                 "flops_per_launch": flops, "flops_per_executed_traj_step": flops / live_steps,
                 "executed_traj_steps": live_steps,
                 "finished_early_frac": 1.0 - live_steps / traj_steps,
+                "lane_steps_run": counts[5], "needed_lane_frac": live_steps / counts[5],
                 "branch_counts": {"beyond_R": counts[0], "shell": counts[1],
                                   "nfw_poly": counts[2], "nfw_log": counts[3]},
                 "full_eval_equiv_tflops": FLOPS_FULL * traj_steps / (kms / 1e3) / 1e12,

@@ -306,15 +306,19 @@ NU_API int nu_batch_kernel_ms(nu_batch* b, float* ms);
  * the trajectory kernel (launched once, synchronously, on `stream`; its
  * results are those of a normal run).  For unfinished trajectories only:
  * counts[0] force evaluations beyond R (gradient exactly zero), counts[1] in
- * the compensating shell, counts[2] in the NFW part with I(y) on its
- * polynomial branch (y < 1), counts[3] on its logarithm branch, counts[4]
- * trajectory-steps integrated.  A trajectory is finished once it lies beyond R
- * and recedes along the integration direction: no later step changes its
- * velocity, so its remaining steps are not needed work (its warp stops when
+ * the compensating shell, counts[2] in the NFW part with I(y) on its first
+ * branch (FP32: the rational approximation, y < min(c, 16); FP64: the series,
+ * y < 1), counts[3] on its logarithm branch, counts[4]
+ * trajectory-steps integrated.  A trajectory is finished once its velocity
+ * can no longer change (it lies beyond R on a line that does not re-enter
+ * before z_end): its remaining steps are not needed work (its warp stops when
  * all of its lanes are finished; the test runs every 4 steps, so up to 3 steps
- * past the finish are counted).  The force is data dependent (App. A has
- * three branches), so these counts turn one run into an exact algorithmic flop
- * count.  counts must hold 5 values.  Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
+ * past the finish are counted).  counts[5] is every lane-step that the warps
+ * ran, finished trajectories and padding lanes included, so counts[4] /
+ * counts[5] is the fraction of lane-steps doing needed work.  The force is
+ * data dependent (App. A has three branches), so these counts turn one run
+ * into an exact algorithmic flop count.  counts must hold 6 values.  Errors:
+ * NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
 NU_API int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts);
 
 /* Launch-shape autotuner: times the batch of requests `hs` with each candidate

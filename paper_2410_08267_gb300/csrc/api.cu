@@ -502,6 +502,7 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
     P.invIc = 1.0 / d.Ic;
     P.invR3 = d.R > 0.0 ? 1.0 / (d.R * d.R * d.R) : 0.0;
     P.R2 = d.R * d.R;
+    P.c_nfw = d.r_s > 0.0 ? d.r200 / d.r_s : 0.0;     // the NFW edge in y
     P.f_p0 = relic->f_p[0];
     P.f_kind = relic->f_kind;
     if (nft > 0) {
@@ -534,9 +535,8 @@ int nu_profile_create(const nu_cosmo* cosmo, const nu_halo* halo, const nu_relic
             put<double>(stage, o_mu, mu.data(), nmu);
             put<double>(stage, o_smu, smu.data(), nmu);
         } else {
-            put<float>(stage, o_coef, coef.data(), coef.size());
-            float* c2 = reinterpret_cast<float*>(stage + o_coef2);
-            for (size_t i = 0; i < coef.size(); ++i) c2[2 * i] = c2[2 * i + 1] = (float)coef[i];
+            fp32_table(coef.data(), N, d, reinterpret_cast<float*>(stage + o_coef),
+                       reinterpret_cast<float*>(stage + o_coef2));
             put<float>(stage, o_x0, x0.data(), n_radii);
             put<float>(stage, o_v0, v0.data(), nq);
             put<float>(stage, o_mu, mu.data(), nmu);
@@ -863,14 +863,14 @@ int nu_batch_branch_counts(nu_batch* b, void* stream, long long* counts)
 {
     if (!b || !counts) return NU_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    constexpr int kTallies = 5;
+    constexpr int kTallies = 6;
     if (!b->d_tallies &&
         cudaMalloc(&b->d_tallies, kTallies * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         b->d_tallies = nullptr;
         return NU_ENOMEM;
     }
-    unsigned long long host[kTallies] = {0, 0, 0, 0, 0};
+    unsigned long long host[kTallies] = {0, 0, 0, 0, 0, 0};
     int rc = NU_OK;
     if (cudaMemsetAsync(b->d_tallies, 0, sizeof(host), s) != cudaSuccess ||
         cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(unsigned), s) != cudaSuccess)

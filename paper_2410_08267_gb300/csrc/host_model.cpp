@@ -149,6 +149,32 @@ double relic_f(const nu_relic& relic, double q)
     return 1.0 / (1.0 + std::exp(q - relic.f_p[0]));
 }
 
+// FP32 copy of the coefficient table, and with dup != nullptr the packed copy
+// with every value stored twice.  The FP32 force tests the NFW edge on y, so
+// the C_Q slots, which hold the squared edge for the FP64 force, carry in the
+// FP32 tables the bound in y below which a lane takes the rational branch of
+// I(y): min(c, kRationalYMax, (1 - 1e-3) R S) with S the stage's
+// 1/((1+z) r_s).  The last term matters only while the NFW edge lies beyond R
+// (before the collapse onset); its factor keeps every lane below the bound
+// inside R whatever the rounding of y.
+void fp32_table(const double* tab, int n_steps, const Derived& d, float* out, float* dup)
+{
+    const double c = d.r_s > 0.0 ? d.r200 / d.r_s : 0.0;
+    const double ymax = std::min(c, kRationalYMax);
+    for (int n = 0; n < n_steps; ++n) {
+        const double* t = tab + (size_t)n * C_COUNT;
+        for (int k = 0; k < C_COUNT; ++k) {
+            double v = t[k];
+            if (k >= C_Q0 && k <= C_Q2)
+                v = std::min(ymax, (1.0 - 1e-3) * d.R * t[C_S0 + (k - C_Q0)]);
+            const float f = (float)v;
+            const size_t j = (size_t)n * C_COUNT + k;
+            if (out) out[j] = f;
+            if (dup) dup[2 * j] = dup[2 * j + 1] = f;
+        }
+    }
+}
+
 // Eq. eoms in u = ln a: dx/du = (1+z)^2 v / H, dv/du = -gradPhi / H with
 // gradPhi = G kappa (1+z) xi M_h Mhat(r,z) x / r^3 (App. A, attractive sign).
 // One RK4 step of size -h needs the stage redshifts at u = -n h, -(n+1/2) h and

@@ -33,6 +33,7 @@ enum CoefSlot {
     C_S1,        // 1/((1+z_m) r_s)
     C_S2,        // 1/((1+z_b) r_s)
     C_Q0,        // min(r200 (1+z_a), R)^2   squared comoving edge of the NFW part
+                 // (FP32 tables: the bound in y of the rational branch, fp32_table)
     C_Q1,
     C_Q2,
     C_T0,        // S(z_a) / I(c)        with rs = S/r: y = r^2 rs, S^2/(I(c) r) = rs T
@@ -68,6 +69,10 @@ double relic_f(const nu_relic& relic, double q);
 // Host tables, written into caller memory (no allocation) or into vectors.
 void coef_table_into(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps,
                      double* table);   // [n_steps][C_COUNT]
+// Largest y of the FP32 force's rational approximation of I(y)/y^2.
+constexpr double kRationalYMax = 16.0;
+// FP32 (and packed FP32) copies of a coefficient table; see host_model.cpp.
+void fp32_table(const double* tab, int n_steps, const Derived& d, float* out, float* dup);
 void coef_table(const nu_cosmo& cosmo, const nu_halo& halo, const Derived& d, int n_steps,
                 std::vector<double>& table);
 void log_nodes_into(int n, double q_min, double q_max, double* q, double* wl, double* wl_coarse);
@@ -102,6 +107,7 @@ struct DevProblem {
     int* status;            // bit 0: non-finite sum
     double q_scale;         // q_i = |v| * q_scale (fiducial mass)
     double invIc, invR3, R2;
+    double c_nfw;           // concentration: the NFW edge in y = r / (r_s (1+z))
     double f_p0;
     int f_kind;
     int n_ftab;             // NU_F_TABLE: nodes of ftab

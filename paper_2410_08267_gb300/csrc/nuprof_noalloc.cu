@@ -213,6 +213,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
     P.invIc = 1.0 / d.Ic;
     P.invR3 = d.R > 0.0 ? 1.0 / (d.R * d.R * d.R) : 0.0;
     P.R2 = d.R * d.R;
+    P.c_nfw = d.r_s > 0.0 ? d.r200 / d.r_s : 0.0;     // the NFW edge in y
     P.f_p0 = relic->f_p[0];
     P.f_kind = relic->f_kind;
     P.n_radii = n_radii;
@@ -235,7 +236,7 @@ extern "C" int nu_profile_compute_noalloc(const nu_cosmo* cosmo, const nu_halo* 
         put_into<double>(st, o_mu, mu, nmu);
         put_into<double>(st, o_smu, smu, nmu);
     } else {
-        put_into<float>(st, o_coef, coef, (size_t)N * C_COUNT);
+        fp32_table(coef, N, d, reinterpret_cast<float*>(st + o_coef), nullptr);
         put_into<float>(st, o_x0, x0, n_radii);
         put_into<float>(st, o_v0, q, nq);
         put_into<float>(st, o_mu, mu, nmu);

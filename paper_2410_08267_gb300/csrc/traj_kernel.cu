@@ -62,23 +62,32 @@ __device__ __forceinline__ float rcp_approx(float v)
     return r;
 }
 
-// I(y) = ln(1+y) - y/(1+y) (Eq. nfw) in FP32.  For y < 1 the two terms cancel,
-// so I = y^2 P(y) with a degree-9 polynomial P fitted to I/y^2 on [0, 1]
-// (nfw_poly_fit.py; 3.5e-7 relative in float32 Horner).  Above, the terms
-// differ by more than a factor 1.5 and are subtracted directly, with the
-// hardware base-2 logarithm and reciprocal (rcp(-u) = -1/u exactly).
-__device__ __forceinline__ float nfw_P(float y)
+// I(y) = ln(1+y) - y/(1+y) (Eq. nfw) in FP32.  For small y the two terms
+// cancel, so inside the NFW part I = y^2 g(y) with g = I/y^2 approximated by a
+// rational function N(y)/D(y) of degrees 4 and 5 on 0 <= y <= 16
+// (nfw_rational_fit.py: 6e-8 relative, 3e-7 after float32 rounding; every
+// coefficient is positive, so neither Horner sum cancels).  It covers the
+// whole NFW part of any halo with c <= 16; above y = 16 (halos with larger c)
+// the two terms differ by more than a factor 1.5 and are subtracted directly,
+// with the hardware base-2 logarithm and reciprocal (rcp(-u) = -1/u exactly).
+__device__ __forceinline__ float nfw_N(float y)
 {
-    float p = -1.933632977e-02f;
-    p = fmaf(p, y, 1.171014905e-01f);
-    p = fmaf(p, y, -3.268344104e-01f);
-    p = fmaf(p, y, 5.741083622e-01f);
-    p = fmaf(p, y, -7.448884845e-01f);
-    p = fmaf(p, y, 8.059346676e-01f);
-    p = fmaf(p, y, -7.959684730e-01f);
-    p = fmaf(p, y, 7.496873736e-01f);
-    p = fmaf(p, y, -6.666569710e-01f);
-    p = fmaf(p, y, 4.999999404e-01f);
+    float p = 3.952767202e-06f;
+    p = fmaf(p, y, 2.387282439e-03f);
+    p = fmaf(p, y, 6.631398201e-02f);
+    p = fmaf(p, y, 3.795046508e-01f);
+    p = fmaf(p, y, 5.000000596e-01f);
+    return p;
+}
+
+__device__ __forceinline__ float nfw_D(float y)
+{
+    float p = 5.989100318e-04f;
+    p = fmaf(p, y, 3.099172190e-02f);
+    p = fmaf(p, y, 3.629413843e-01f);
+    p = fmaf(p, y, 1.422382593e+00f);
+    p = fmaf(p, y, 2.092346668e+00f);
+    p = fmaf(p, y, 1.0f);
     return p;
 }
 
@@ -137,28 +146,33 @@ __device__ __forceinline__ bool escapes(T r2, T dot, T v2, T R2, T R, T irem)
     return r2 >= kMiss * (reach * reach);
 }
 
-struct HaloF32 { float invIc, invR3, R2, R; };
+// c: the NFW edge r = r200 (1+z) in y = r S.
+struct HaloF32 { float invIc, invR3, R2, R, c; };
 struct HaloF64 { double invIc, invR3, R2, R; };
 
 // Branch tallies of force evaluations, kept only by the counting variant of the
 // kernel (used once, untimed, to turn the data-dependent work into an exact
-// algorithmic flop count): beyond R, shell, NFW part on the polynomial branch
-// of I(y), NFW part on the logarithm branch, and the trajectory-steps of
+// algorithmic flop count): beyond R, shell, NFW part on the first branch of
+// I(y) (FP32: the rational function; FP64: the series), NFW part on the
+// logarithm branch, and the trajectory-steps of
 // unfinished trajectories.  Steps that a finished trajectory runs only because
-// its warp is still busy are not counted (they are not needed work).
+// its warp is still busy are not counted (they are not needed work); the sixth
+// count is every lane-step the warps ran, needed or not (padding lanes too).
 struct NoTally {
     __device__ __forceinline__ void add(int) {}
     __device__ __forceinline__ void set_live(bool) {}
+    __device__ __forceinline__ void ran(unsigned) {}
 };
 struct Tally {
-    unsigned n[5] = {0u, 0u, 0u, 0u, 0u};   // 4 branches + live trajectory-steps
-    bool live = true;                       // only unfinished trajectories count
+    unsigned n[6] = {0u, 0u, 0u, 0u, 0u, 0u};   // 4 branches, live steps, lane-steps run
+    bool live = true;                           // only unfinished trajectories count
     __device__ __forceinline__ void add(int k) { n[k] += live ? 1u : 0u; }
     __device__ __forceinline__ void set_live(bool v)
     {
         live = v;
         n[4] += v ? 1u : 0u;
     }
+    __device__ __forceinline__ void ran(unsigned k) { n[5] += k; }
 };
 
 // The compensated halo's gradient vanishes beyond R, and the NFW term only
@@ -170,11 +184,16 @@ struct Tally {
 // (scalar, packed, any warp composition) gives a lane the same bits.  With
 // rs = S/r and the table's T = S/I(c) (so y = r S = r^2 rs):
 //   beyond R:              m = 0
-//   NFW, y < 1:            m = P(y) (rs T) - 1/R^3
-//                          (I rinv^3 / I(c) = y^2 P rinv^3 / I(c) = P S^2 rinv / I(c))
-//   NFW, y >= 1:           m = (I(y)/I(c)) rinv^3 - 1/R^3
+//   NFW, y < Yq:           m = (N(y) (rs T)) rcp(D(y)) - 1/R^3
+//                          (I rinv^3 / I(c) = y^2 g rinv^3 / I(c) = g S^2 rinv / I(c))
+//   NFW, Yq <= y < c:      m = (I(y)/I(c)) rinv^3 - 1/R^3
 //   shell:                 m = rinv^2 rinv - 1/R^3 (one rounding)
-// The table guarantees Q <= R^2, so r^2 < Q implies r^2 < R^2.
+// Yq, the stage's bound of the rational branch (the FP32 table's C_Q slots),
+// is min(c, 16, (1 - 1e-3) R S): y < Yq implies r < R with a margin far above
+// the rounding of y, so that one compare classifies a lane.  The NFW part is
+// y < c (the edge r = r200 (1+z) is y = c exactly), tested on y itself; the
+// FP64 path tests r^2 against the table's squared edge.  The two tests differ
+// only in the rounding at the edge, where the mass is continuous.
 // The r -> 0 guard is folded into r^2 itself: r^2 = x^2 + (y^2 + 1e-20) with
 // two fused multiply-adds, which changes the bits of r^2 only below ~2e-13 kpc^2.
 __device__ __forceinline__ float guarded_r2(float x, float y)
@@ -183,7 +202,7 @@ __device__ __forceinline__ float guarded_r2(float x, float y)
 }
 
 template <class Ctr = NoTally>
-__device__ __forceinline__ float accel_m(float x, float y, float S, float Q, float T,
+__device__ __forceinline__ float accel_m(float x, float y, float S, float Yq, float T,
                                          const HaloF32& hc, Ctr& ctr)
 {
     const float r2 = guarded_r2(x, y);
@@ -192,12 +211,12 @@ __device__ __forceinline__ float accel_m(float x, float y, float S, float Q, flo
         const float rinv = rsqrt_approx(r2);
         const float rs = rinv * S;
         const float ys = r2 * rs;
-        if (r2 < Q && ys < 1.0f) {
+        if (ys < Yq) {
             ctr.add(2);
-            m = fmaf(nfw_P(ys), rs * T, -hc.invR3);
+            m = fmaf(nfw_N(ys) * (rs * T), rcp_approx(nfw_D(ys)), -hc.invR3);
         } else {
             const float rinv2 = rinv * rinv;
-            if (r2 < Q) {
+            if (ys < hc.c) {
                 ctr.add(3);
                 const float sel = nfw_I_log(ys, fmaf(r2, rs, 1.0f)) * hc.invIc;
                 m = fmaf(sel, rinv2 * rinv, -hc.invR3);
@@ -241,7 +260,7 @@ template <> struct PrecTraits<float> {
     using Halo = HaloF32;
     static __device__ __forceinline__ Halo halo(const DevProblem& P)
     {
-        return {(float)P.invIc, (float)P.invR3, (float)P.R2, (float)sqrt(P.R2)};
+        return {(float)P.invIc, (float)P.invR3, (float)P.R2, (float)sqrt(P.R2), (float)P.c_nfw};
     }
 };
 template <> struct PrecTraits<double> {
@@ -384,22 +403,27 @@ __device__ __forceinline__ f2 dup(float a) { return pk(a, a); }
 
 struct HaloX2 {
     f2 invIc, neg_invR3;
-    float R2;
+    float R2, c;
 };
 
-// P(y) = I(y)/y^2 on the polynomial branch for both lanes (see nfw_P).
-__device__ __forceinline__ f2 nfw_P_x2(f2 y)
+// N(y) and D(y) of the rational g for both lanes (see nfw_N, nfw_D).
+__device__ __forceinline__ f2 nfw_N_x2(f2 y)
 {
-    f2 p = dup(-1.933632977e-02f);
-    p = fma2(p, y, dup(1.171014905e-01f));
-    p = fma2(p, y, dup(-3.268344104e-01f));
-    p = fma2(p, y, dup(5.741083622e-01f));
-    p = fma2(p, y, dup(-7.448884845e-01f));
-    p = fma2(p, y, dup(8.059346676e-01f));
-    p = fma2(p, y, dup(-7.959684730e-01f));
-    p = fma2(p, y, dup(7.496873736e-01f));
-    p = fma2(p, y, dup(-6.666569710e-01f));
-    p = fma2(p, y, dup(4.999999404e-01f));
+    f2 p = dup(3.952767202e-06f);
+    p = fma2(p, y, dup(2.387282439e-03f));
+    p = fma2(p, y, dup(6.631398201e-02f));
+    p = fma2(p, y, dup(3.795046508e-01f));
+    p = fma2(p, y, dup(5.000000596e-01f));
+    return p;
+}
+__device__ __forceinline__ f2 nfw_D_x2(f2 y)
+{
+    f2 p = dup(5.989100318e-04f);
+    p = fma2(p, y, dup(3.099172190e-02f));
+    p = fma2(p, y, dup(3.629413843e-01f));
+    p = fma2(p, y, dup(1.422382593e+00f));
+    p = fma2(p, y, dup(2.092346668e+00f));
+    p = fma2(p, y, dup(1.0f));
     return p;
 }
 
@@ -413,31 +437,31 @@ __device__ __forceinline__ f2 nfw_I_log_x2(f2 y, f2 u)
 }
 
 // Geometry of one force evaluation for both lanes of a register pair:
-// guarded r^2, 1/r, rs = S/r and y = r^2 rs, and the lane classes (inside the
-// NFW edge; on the polynomial branch of I(y)).
+// guarded r^2, 1/r, rs = S/r and y = r^2 rs, and per lane whether it is on
+// the rational branch of the NFW part (y < Yq, which implies r < R).
 struct Geo2 {
     f2 r2, rinv, rs, ys;
-    bool n0, n1, p0, p1;
+    bool q0, q1;
 };
 
-__device__ __forceinline__ Geo2 geometry_x2(f2 x, f2 y, f2 S, f2 Q)
+__device__ __forceinline__ Geo2 geometry_x2(f2 x, f2 y, f2 S, f2 Yq)
 {
     Geo2 g;
     g.r2 = fma2(x, x, fma2(y, y, dup(kR2Guard)));
     g.rinv = pk(rsqrt_approx(f2lo(g.r2)), rsqrt_approx(f2hi(g.r2)));
     g.rs = mul2(g.rinv, S);
     g.ys = mul2(g.r2, g.rs);
-    g.n0 = f2lo(g.r2) < f2lo(Q);
-    g.n1 = f2hi(g.r2) < f2hi(Q);
-    g.p0 = g.n0 && f2lo(g.ys) < 1.0f;
-    g.p1 = g.n1 && f2hi(g.ys) < 1.0f;
+    g.q0 = f2lo(g.ys) < f2lo(Yq);
+    g.q1 = f2hi(g.ys) < f2hi(Yq);
     return g;
 }
 
 // Per-branch formulas of accel_m for both lanes (FP32, the same operations).
-__device__ __forceinline__ f2 m_poly_x2(const Geo2& g, f2 T, const HaloX2& hc)
+__device__ __forceinline__ f2 m_rational_x2(const Geo2& g, f2 T, const HaloX2& hc)
 {
-    return fma2(nfw_P_x2(g.ys), mul2(g.rs, T), hc.neg_invR3);
+    const f2 nr = mul2(nfw_N_x2(g.ys), mul2(g.rs, T));
+    const f2 d = nfw_D_x2(g.ys);
+    return fma2(nr, pk(rcp_approx(f2lo(d)), rcp_approx(f2hi(d))), hc.neg_invR3);
 }
 __device__ __forceinline__ f2 m_log_x2(const Geo2& g, f2 rinv2, const HaloX2& hc)
 {
@@ -454,15 +478,18 @@ __device__ __forceinline__ f2 m_out_x2(const Geo2& g, const HaloX2& hc)
     const f2 ms = m_shell_x2(g, mul2(g.rinv, g.rinv), hc);
     return pk(f2lo(g.r2) < hc.R2 ? f2lo(ms) : 0.0f, f2hi(g.r2) < hc.R2 ? f2hi(ms) : 0.0f);
 }
-// any mix of branches: each formula for both lanes, selected per lane
-__device__ __forceinline__ f2 m_mixed_x2(const Geo2& g, f2 T, const HaloX2& hc)
+// any mix of branches: each formula that some lane of the warp needs,
+// evaluated for both lanes and selected per lane
+__device__ __forceinline__ f2 m_mixed_x2(const Geo2& g, f2 T, const HaloX2& hc, bool need_log)
 {
     const f2 rinv2 = mul2(g.rinv, g.rinv);
-    const f2 mp = m_poly_x2(g, T, hc);
-    const f2 ml = m_log_x2(g, rinv2, hc);
+    const f2 mq = m_rational_x2(g, T, hc);
+    const f2 ml = need_log ? m_log_x2(g, rinv2, hc) : dup(0.0f);
     const f2 ms = m_shell_x2(g, rinv2, hc);
-    return pk(g.p0 ? f2lo(mp) : g.n0 ? f2lo(ml) : (f2lo(g.r2) < hc.R2 ? f2lo(ms) : 0.0f),
-              g.p1 ? f2hi(mp) : g.n1 ? f2hi(ml) : (f2hi(g.r2) < hc.R2 ? f2hi(ms) : 0.0f));
+    const bool n0 = f2lo(g.ys) < hc.c, n1 = f2hi(g.ys) < hc.c;
+    const bool in0 = f2lo(g.r2) < hc.R2, in1 = f2hi(g.r2) < hc.R2;
+    return pk(!in0 ? 0.0f : g.q0 ? f2lo(mq) : n0 ? f2lo(ml) : f2lo(ms),
+              !in1 ? 0.0f : g.q1 ? f2hi(mq) : n1 ? f2hi(ml) : f2hi(ms));
 }
 
 // m = Mhat/r^3 at two independent points (a, b) of both lanes: lane by lane
@@ -471,36 +498,39 @@ __device__ __forceinline__ f2 m_mixed_x2(const Geo2& g, f2 T, const HaloX2& hc)
 // given the first two, so their force evaluations are independent and run
 // interleaved.  One warp vote covers all four lane-evaluations (the two
 // points of a pair almost always share their branch): every one on the
-// polynomial branch of the NFW part (the common case), every one on its
-// logarithm branch, every one outside the NFW edge (shell or beyond R), or
-// any mix (each formula evaluated and selected per lane).  All lanes of the
-// warp execute this function together (the integration loop is warp-uniform).
-__device__ __forceinline__ void accel_m_pair_x2(f2 xa, f2 ya, f2 Sa, f2 Qa, f2 Ta,
-                                                f2 xb, f2 yb, f2 Sb, f2 Qb, f2 Tb,
+// rational branch of the NFW part (the common case: it covers the whole NFW
+// part of halos with c <= 16), every one outside the NFW edge (shell or
+// beyond R), or any mix (each formula that a lane needs evaluated for all and
+// selected per lane).  All lanes of the warp execute this function together
+// (the integration loop is warp-uniform).
+__device__ __forceinline__ void accel_m_pair_x2(f2 xa, f2 ya, f2 Sa, f2 Ya, f2 Ta,
+                                                f2 xb, f2 yb, f2 Sb, f2 Yb, f2 Tb,
                                                 const HaloX2& hc, f2& ma, f2& mb)
 {
-    const Geo2 ga = geometry_x2(xa, ya, Sa, Qa);
-    const Geo2 gb = geometry_x2(xb, yb, Sb, Qb);
+    const Geo2 ga = geometry_x2(xa, ya, Sa, Ya);
+    const Geo2 gb = geometry_x2(xb, yb, Sb, Yb);
     const unsigned full = 0xffffffffu;
-    if (__all_sync(full, ga.p0 && ga.p1 && gb.p0 && gb.p1)) {
-        ma = m_poly_x2(ga, Ta, hc);
-        mb = m_poly_x2(gb, Tb, hc);
+    if (__all_sync(full, ga.q0 && ga.q1 && gb.q0 && gb.q1)) {
+        ma = m_rational_x2(ga, Ta, hc);
+        mb = m_rational_x2(gb, Tb, hc);
         return;
     }
-    const bool nall = ga.n0 && ga.n1 && gb.n0 && gb.n1;
-    const bool pany = ga.p0 || ga.p1 || gb.p0 || gb.p1;
-    if (__all_sync(full, nall && !pany)) {
-        ma = m_log_x2(ga, mul2(ga.rinv, ga.rinv), hc);
-        mb = m_log_x2(gb, mul2(gb.rinv, gb.rinv), hc);
-        return;
-    }
-    if (__all_sync(full, !(ga.n0 || ga.n1 || gb.n0 || gb.n1))) {
+    // lanes inside R and inside the NFW edge
+    const bool na0 = f2lo(ga.r2) < hc.R2 && f2lo(ga.ys) < hc.c;
+    const bool na1 = f2hi(ga.r2) < hc.R2 && f2hi(ga.ys) < hc.c;
+    const bool nb0 = f2lo(gb.r2) < hc.R2 && f2lo(gb.ys) < hc.c;
+    const bool nb1 = f2hi(gb.r2) < hc.R2 && f2hi(gb.ys) < hc.c;
+    if (__all_sync(full, !(na0 || na1 || nb0 || nb1))) {
         ma = m_out_x2(ga, hc);
         mb = m_out_x2(gb, hc);
         return;
     }
-    ma = m_mixed_x2(ga, Ta, hc);
-    mb = m_mixed_x2(gb, Tb, hc);
+    // a lane of the NFW part above the rational branch (only halos with c > 16)
+    const bool la = (na0 && !ga.q0) || (na1 && !ga.q1);
+    const bool lb = (nb0 && !gb.q0) || (nb1 && !gb.q1);
+    const bool need_log = __any_sync(full, la || lb);
+    ma = m_mixed_x2(ga, Ta, hc, need_log);
+    mb = m_mixed_x2(gb, Tb, hc, need_log);
 }
 
 // One 16-byte entry of the duplicated table (two slots, each a {c, c} pair).
@@ -526,9 +556,9 @@ __device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const 
     const f2 X2 = fma2(MA1, vx, x), Y2 = fma2(MA1, vy, y);
     const ulonglong2 q5 = coef_pair<GTAB>(src4, 5), q6 = coef_pair<GTAB>(src4, 6);
     const ulonglong2 q7 = coef_pair<GTAB>(src4, 7), q8 = coef_pair<GTAB>(src4, 8);
-    const f2 S0{q5.x}, S1{q5.y}, Q0{q6.y}, Q1{q7.x}, T0{q8.x}, T1{q8.y};
+    const f2 S0{q5.x}, S1{q5.y}, Yq0{q6.y}, Yq1{q7.x}, T0{q8.x}, T1{q8.y};
     f2 m1, m2;
-    accel_m_pair_x2(x, y, S0, Q0, T0, X2, Y2, S1, Q1, T1, hc, m1, m2);
+    accel_m_pair_x2(x, y, S0, Yq0, T0, X2, Y2, S1, Yq1, T1, hc, m1, m2);
     const ulonglong2 q1 = coef_pair<GTAB>(src4, 1), q2 = coef_pair<GTAB>(src4, 2);
     const f2 MA3{q1.x}, B1{q1.y}, B2{q2.x};
     const f2 p1 = mul2(B1, m1);
@@ -539,9 +569,9 @@ __device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const 
     const f2 X4 = fma2(MA3, VX3, x), Y4 = fma2(MA3, VY3, y);
 
     const ulonglong2 q9 = coef_pair<GTAB>(src4, 9);
-    const f2 S2{q6.x}, Q2{q7.y}, T2{q9.x};
+    const f2 S2{q6.x}, Yq2{q7.y}, T2{q9.x};
     f2 m3, m4;
-    accel_m_pair_x2(X3, Y3, S1, Q1, T1, X4, Y4, S2, Q2, T2, hc, m3, m4);
+    accel_m_pair_x2(X3, Y3, S1, Yq1, T1, X4, Y4, S2, Yq2, T2, hc, m3, m4);
     const ulonglong2 q3 = coef_pair<GTAB>(src4, 3), q4 = coef_pair<GTAB>(src4, 4);
     const f2 B3{q2.y}, B4{q3.x}, W0{q3.y}, W1{q4.x}, W2{q4.y};
     const f2 p3 = mul2(B3, m3);
@@ -732,7 +762,7 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             static_assert(TPT == 2, "packed path holds two trajectories");
             f2 X = pk(x[0], x[1]), Y = pk(y[0], y[1]);
             f2 VX = pk(vx[0], vx[1]), VY = pk(vy[0], vy[1]);
-            const HaloX2 h2{dup(hc.invIc), dup(-hc.invR3), hc.R2};
+            const HaloX2 h2{dup(hc.invIc), dup(-hc.invR3), hc.R2, hc.c};
             for (int n = s_begin; n < s_end; ++n) {
                 if (((n - s_begin) & (kExitEvery - 1)) == 0) {
                     const f2 r2 = fma2(X, X, mul2(Y, Y));
@@ -769,6 +799,7 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
                     done |= fin;
                     if (__all_sync(0xffffffffu, done)) break;
                 }
+                ctr.ran(TPT);
                 T c[C_COUNT];
                 const float4* c4 = reinterpret_cast<const float4*>(tab + (size_t)n * C_COUNT);
 #pragma unroll
@@ -894,7 +925,7 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
     }
     if constexpr (COUNT) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < 6; ++k) {
             unsigned long long v = ctr.n[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -421,7 +421,7 @@ def nu_batch_info(b) -> dict:
 
 
 def nu_batch_branch_counts(b, stream=None):
-    counts = (C.c_longlong * 5)()
+    counts = (C.c_longlong * 6)()
     _check(lib().nu_batch_branch_counts(b, _stream_ptr(stream), counts), "nu_batch_branch_counts")
     return [int(v) for v in counts]
 

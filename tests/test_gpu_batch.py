@@ -120,7 +120,12 @@ def test_batch_tile_override_matches_handles_of_that_shape():
 
 
 def test_branch_counts_are_exact():
+    """Exact tallies of one counting run.  In the mixed mode the rational
+    approximation of I(y) covers the whole NFW part of a halo with c <= 16, so
+    its logarithm branch (counts[3]) is taken only for a more concentrated
+    halo, above y = 16."""
     probs = [W.plain_small(precision=W.MIXED)[0].replace(n_steps=50),
+             W.plain_small(precision=W.MIXED)[0].replace(n_steps=50, c=25.0),
              W.plain_small(precision=W.MIXED)[0].replace(n_steps=50, M_h=0.0)]
     for pb in probs:
         h = nu.create(pb)
@@ -129,10 +134,15 @@ def test_branch_counts_are_exact():
             c = nu.nu_batch_branch_counts(b)
             # four force evaluations per integrated step of an unfinished trajectory
             assert sum(c[:4]) == 4 * c[4] and c[4] <= pb.n_steps * pb.n_traj
+            # every needed step is one of the lane-steps run, which come in
+            # whole warps
+            assert c[4] <= c[5] and c[5] % 32 == 0
             if pb.M_h == 0.0:
                 # no halo (R = 0): every straight path stays outside R, so
                 # every trajectory is finished before its first step
-                assert c == [0, 0, 0, 0, 0]
+                assert c == [0, 0, 0, 0, 0, 0]
+            elif pb.c <= 16.0:
+                assert c[3] == 0 and min(c[:3] + c[4:]) > 0
             else:
                 assert min(c) > 0
             # the counting launch leaves results alone; a normal run still works

@@ -197,7 +197,8 @@ def test_precision_sweep_full_size_sampled_radii(prec):
 def test_packed_path_is_bitwise_the_two_trajectory_path(block):
     """The packed FP32x2 path performs the scalar two-trajectory path's
     operations lane by lane: identical n/nbar, error estimate and q_i."""
-    cases = [W.plain_small(precision=W.MIXED)[0]] + W.random_small(6, n=4, precision=W.MIXED)
+    cases = ([W.plain_small(precision=W.MIXED)[0], W.plain_small(precision=W.MIXED)[0].replace(c=25.0)]
+             + W.random_small(6, n=4, precision=W.MIXED))
     for pb in cases:
         outs = []
         for tpt in (2, 3):
@@ -211,6 +212,23 @@ def test_packed_path_is_bitwise_the_two_trajectory_path(block):
                 nu.nu_profile_destroy(h)
         for a, b in zip(outs[0], outs[1]):
             assert np.array_equal(a, b)
+
+
+def test_concentrated_halo_takes_the_logarithm_above_the_rational_range():
+    """Mixed mode, c = 25: the FP32 force's rational approximation of I(y)/y^2
+    ends at y = 16, so the inner NFW part takes the rational branch, the part
+    16 <= y < 25 the logarithm branch, and warps whose lanes straddle the
+    bound evaluate both; n/nbar against the oracle at every radius."""
+    pb = W.plain_small(precision=W.MIXED)[0].replace(c=25.0)
+    h = nu.create(pb)
+    b = nu.nu_batch_create([h])
+    try:
+        c = nu.nu_batch_branch_counts(b)
+    finally:
+        nu.nu_batch_destroy(b)
+        nu.nu_profile_destroy(h)
+    assert c[2] > 0 and c[3] > 0, c
+    assert_parity(nu.profile(pb)[0], pb, where="c = 25", min_checked=pb.n_radii // 2)
 
 
 @pytest.mark.parametrize("prec", [W.FP64, W.MIXED])
