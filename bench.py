@@ -61,11 +61,11 @@ SMS, FP32_LANES_PER_SM = 152, 128
 # (dram__bytes_read.sum + dram__bytes_write.sum), recorded in
 # profiles/traj_kernel_precision_sweep_mixed.md.  Must be reset to None
 # whenever the kernel changes, until it is captured again.
-NCU_TRAFFIC_BYTES = {"128x3xg": 1289472.0}
+NCU_TRAFFIC_BYTES = {"128x3xg": 1227520.0}
 # Pipe utilisation of the same kernel and shape on this workload, from one-pass
 # ncu captures (sm__pipe_fma_cycles_active, smsp__issue_active), also recorded
 # in that profile summary; reset together with the traffic when the kernel changes.
-NCU_PIPES = {"128x3xg": {"fma_pipe_cycles_active": 0.625, "issue_slots_active": 0.656}}
+NCU_PIPES = {"128x3xg": {"fma_pipe_cycles_active": 0.680, "issue_slots_active": 0.615}}
 SAMPLE_RADII = (0, 9, 18, 27, 36, 45, 54, 63)   # oracle sample: ~1 s on 16 cores
 SAMPLE_MASS_INDEX = 2          # 0.1 eV
 
@@ -382,6 +382,8 @@ def bench_ours(args):
     one = W.precision_sweep(precision=prec)
     if args.case == "small":            # profiling case: one mass, 24 radii (fills every SM)
         one = [one[SAMPLE_MASS_INDEX].replace(radii=np.geomspace(1.0, 1000.0, 24))]
+    elif args.case == "medium":         # profiling case: every mass, every 4th radius
+        one = [pb.replace(radii=pb.radii[::4]) for pb in one]
     elif args.case == "uneven":         # 1024 halos of uneven sizes in one launch
         one = W.batched_uneven(precision=prec)
     elif args.case == "new_physics":    # 256 halos, relic kinds and couplings
@@ -631,6 +633,8 @@ def bench_ours(args):
 
     if args.case == "small":
         WORKLOAD_USED = "small profiling case of " + WORKLOAD + " (m_nu=0.1 eV, 24 radii)"
+    elif args.case == "medium":
+        WORKLOAD_USED = "medium profiling case of " + WORKLOAD + " (every 4th radius: 16 of 64)"
     elif args.case == "uneven":
         WORKLOAD_USED = ("batched_uneven: 1024 halos (seed 2410), log10 M ~ U[11,15], n_r ~ U{8..128} "
                          "x n_q ~ U{32..256} x n_mu ~ U{16..64}, linear growth, 400 RK4 steps z 0->4")
@@ -703,8 +707,9 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--shape", default="auto",
                     help="launch shape BLOCKxTPT[xg] (e.g. 256x1, 256x3xg), or auto (autotuner)")
-    ap.add_argument("--case", choices=("full", "small", "uneven", "new_physics"), default="full",
-                    help="small: one mass x 24 radii of the same workload, for profiler captures; "
+    ap.add_argument("--case", choices=("full", "small", "medium", "uneven", "new_physics"), default="full",
+                    help="small: one mass x 24 radii of the same workload; medium: all four masses, "
+                         "every 4th radius (the full workload's branch mix), both for profiler captures; "
                          "uneven / new_physics: the 1024-halo and 256-halo batch workloads")
     ap.add_argument("--serve-rate", type=float, default=300.0,
                     help="request rate of the serving leg (0: skip it)")
