@@ -197,7 +197,9 @@ def test_precision_sweep_full_size_sampled_radii(prec):
 def test_packed_path_is_bitwise_the_two_trajectory_path(block):
     """The packed FP32x2 path performs the scalar two-trajectory path's
     operations lane by lane: identical n/nbar, error estimate and q_i."""
-    cases = ([W.plain_small(precision=W.MIXED)[0], W.plain_small(precision=W.MIXED)[0].replace(c=25.0)]
+    base = W.plain_small(precision=W.MIXED)[0]
+    cases = ([base, base.replace(c=25.0), base.replace(c=0.5),
+              base.replace(xi_kind=W.XI_STATIC, z_end=6.0)]
              + W.random_small(6, n=4, precision=W.MIXED))
     for pb in cases:
         outs = []
@@ -229,6 +231,25 @@ def test_concentrated_halo_takes_the_logarithm_above_the_rational_range():
         nu.nu_profile_destroy(h)
     assert c[2] > 0 and c[3] > 0, c
     assert_parity(nu.profile(pb)[0], pb, where="c = 25", min_checked=pb.n_radii // 2)
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.MIXED])
+def test_integration_past_the_collapse_onset(prec):
+    """z_end = 6, beyond z_i = 4.85, for a halo that exists there (static
+    growth): the NFW edge r200 (1+z) then lies beyond R, nothing acts beyond
+    R, and in the FP32 force the rational branch's bound takes its R S term.
+    n/nbar against the oracle at every radius."""
+    pb = W.plain_small(precision=prec)[0].replace(xi_kind=W.XI_STATIC, z_end=6.0)
+    assert oracle.derive(pb)["z_i"] < pb.z_end
+    assert_parity(nu.profile(pb)[0], pb, where="past z_i", min_checked=pb.n_radii // 2)
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.MIXED])
+def test_concentration_below_one(prec):
+    """c = 0.5: the NFW edge y = c lies below 1, so the whole NFW part is on
+    the first branch of I(y) and its edge, not y = 1, ends it."""
+    pb = W.plain_small(precision=prec)[0].replace(c=0.5)
+    assert_parity(nu.profile(pb)[0], pb, where="c = 0.5", min_checked=pb.n_radii // 2)
 
 
 @pytest.mark.parametrize("prec", [W.FP64, W.MIXED])
