@@ -599,7 +599,7 @@ def bench_ours(args):
                 "finished_early_frac": 1.0 - live_steps / traj_steps,
                 "lane_steps_run": counts[5], "needed_lane_frac": live_steps / counts[5],
                 "branch_counts": {"beyond_R": counts[0], "shell": counts[1],
-                                  "nfw_poly": counts[2], "nfw_log": counts[3]},
+                                  "nfw_rational_or_series": counts[2], "nfw_log": counts[3]},
                 "full_eval_equiv_tflops": FLOPS_FULL * traj_steps / (kms / 1e3) / 1e12,
                 "peak_basis": peak_basis}
 
