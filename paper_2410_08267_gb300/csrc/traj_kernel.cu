@@ -64,13 +64,17 @@ __device__ __forceinline__ float rcp_approx(float v)
 
 // I(y) = ln(1+y) - y/(1+y) (Eq. nfw) in FP32.  For small y the two terms
 // cancel, so inside the NFW part I = y^2 g(y) with g = I/y^2 approximated by a
-// rational function N(y)/D(y) of degrees 4 and 5 on 0 <= y <= 16
-// (nfw_rational_fit.py: 6e-8 relative, 3e-7 after float32 rounding; every
-// coefficient is positive, so neither Horner sum cancels).  It covers the
-// whole NFW part of any halo with c <= 16; above y = 16 (halos with larger c)
-// the two terms differ by more than a factor 1.5 and are subtracted directly,
-// with the hardware base-2 logarithm and reciprocal (rcp(-u) = -1/u exactly).
-__device__ __forceinline__ float nfw_N(float y)
+// rational function N(y)/D(y) (nfw_rational_fit.py).  Two fits exist, and a
+// request uses one of them for all of its evaluations:
+//   wide:   degrees 4 and 5 on 0 <= y <= 16 (6e-8 relative, 3e-7 after float32
+//           rounding; every coefficient positive), for halos with c > 8;
+//   narrow: degrees 4 and 4 on 0 <= y <= 8 (6e-8, 3e-7), one fused
+//           multiply-add cheaper, for halos with c <= 8, whose NFW part never
+//           reaches y = 8.
+// Above y = 16 (halos with c > 16) the two terms differ by more than a factor
+// 1.5 and are subtracted directly, with the hardware base-2 logarithm and
+// reciprocal (rcp(-u) = -1/u exactly).
+__device__ __forceinline__ float nfw_N16(float y)
 {
     float p = 3.952767202e-06f;
     p = fmaf(p, y, 2.387282439e-03f);
@@ -80,7 +84,7 @@ __device__ __forceinline__ float nfw_N(float y)
     return p;
 }
 
-__device__ __forceinline__ float nfw_D(float y)
+__device__ __forceinline__ float nfw_D16(float y)
 {
     float p = 5.989100318e-04f;
     p = fmaf(p, y, 3.099172190e-02f);
@@ -90,6 +94,29 @@ __device__ __forceinline__ float nfw_D(float y)
     p = fmaf(p, y, 1.0f);
     return p;
 }
+
+__device__ __forceinline__ float nfw_N8(float y)
+{
+    float p = -4.539978363e-06f;
+    p = fmaf(p, y, 4.568357544e-04f);
+    p = fmaf(p, y, 4.554858804e-02f);
+    p = fmaf(p, y, 3.421576917e-01f);
+    p = fmaf(p, y, 5.000000000e-01f);
+    return p;
+}
+
+__device__ __forceinline__ float nfw_D8(float y)
+{
+    float p = 1.647129469e-02f;
+    p = fmaf(p, y, 2.829689085e-01f);
+    p = fmaf(p, y, 1.281258702e+00f);
+    p = fmaf(p, y, 2.017652512e+00f);
+    p = fmaf(p, y, 1.0f);
+    return p;
+}
+
+// Largest concentration served by the narrow fit.
+constexpr float kNarrowMaxC = 8.0f;
 
 // y = r^2 rs is passed together with u = 1 + y formed as one fused
 // multiply-add from r^2 and rs (every FP32 product that feeds a sum is written
@@ -146,8 +173,9 @@ __device__ __forceinline__ bool escapes(T r2, T dot, T v2, T R2, T R, T irem)
     return r2 >= kMiss * (reach * reach);
 }
 
-// c: the NFW edge r = r200 (1+z) in y = r S.
-struct HaloF32 { float invIc, invR3, R2, R, c; };
+// c: the NFW edge r = r200 (1+z) in y = r S; narrow: c <= 8, the request uses
+// the narrow rational fit.
+struct HaloF32 { float invIc, invR3, R2, R, c; bool narrow; };
 struct HaloF64 { double invIc, invR3, R2, R; };
 
 // Branch tallies of force evaluations, kept only by the counting variant of the
@@ -213,7 +241,9 @@ __device__ __forceinline__ float accel_m(float x, float y, float S, float Yq, fl
         const float ys = r2 * rs;
         if (ys < Yq) {
             ctr.add(2);
-            m = fmaf(nfw_N(ys) * (rs * T), rcp_approx(nfw_D(ys)), -hc.invR3);
+            const float n = hc.narrow ? nfw_N8(ys) : nfw_N16(ys);
+            const float d = hc.narrow ? nfw_D8(ys) : nfw_D16(ys);
+            m = fmaf(n * (rs * T), rcp_approx(d), -hc.invR3);
         } else {
             const float rinv2 = rinv * rinv;
             if (ys < hc.c) {
@@ -260,7 +290,8 @@ template <> struct PrecTraits<float> {
     using Halo = HaloF32;
     static __device__ __forceinline__ Halo halo(const DevProblem& P)
     {
-        return {(float)P.invIc, (float)P.invR3, (float)P.R2, (float)sqrt(P.R2), (float)P.c_nfw};
+        const float c = (float)P.c_nfw;
+        return {(float)P.invIc, (float)P.invR3, (float)P.R2, (float)sqrt(P.R2), c, c <= kNarrowMaxC};
     }
 };
 template <> struct PrecTraits<double> {
@@ -406,24 +437,45 @@ struct HaloX2 {
     float R2, c;
 };
 
-// N(y) and D(y) of the rational g for both lanes (see nfw_N, nfw_D).
+// N(y) and D(y) of the rational g for both lanes (see nfw_N16, nfw_D16 and
+// nfw_N8, nfw_D8); NARROW selects the fit.
+template <bool NARROW>
 __device__ __forceinline__ f2 nfw_N_x2(f2 y)
 {
-    f2 p = dup(3.952767202e-06f);
-    p = fma2(p, y, dup(2.387282439e-03f));
-    p = fma2(p, y, dup(6.631398201e-02f));
-    p = fma2(p, y, dup(3.795046508e-01f));
-    p = fma2(p, y, dup(5.000000596e-01f));
+    f2 p;
+    if constexpr (NARROW) {
+        p = dup(-4.539978363e-06f);
+        p = fma2(p, y, dup(4.568357544e-04f));
+        p = fma2(p, y, dup(4.554858804e-02f));
+        p = fma2(p, y, dup(3.421576917e-01f));
+        p = fma2(p, y, dup(5.000000000e-01f));
+    } else {
+        p = dup(3.952767202e-06f);
+        p = fma2(p, y, dup(2.387282439e-03f));
+        p = fma2(p, y, dup(6.631398201e-02f));
+        p = fma2(p, y, dup(3.795046508e-01f));
+        p = fma2(p, y, dup(5.000000596e-01f));
+    }
     return p;
 }
+template <bool NARROW>
 __device__ __forceinline__ f2 nfw_D_x2(f2 y)
 {
-    f2 p = dup(5.989100318e-04f);
-    p = fma2(p, y, dup(3.099172190e-02f));
-    p = fma2(p, y, dup(3.629413843e-01f));
-    p = fma2(p, y, dup(1.422382593e+00f));
-    p = fma2(p, y, dup(2.092346668e+00f));
-    p = fma2(p, y, dup(1.0f));
+    f2 p;
+    if constexpr (NARROW) {
+        p = dup(1.647129469e-02f);
+        p = fma2(p, y, dup(2.829689085e-01f));
+        p = fma2(p, y, dup(1.281258702e+00f));
+        p = fma2(p, y, dup(2.017652512e+00f));
+        p = fma2(p, y, dup(1.0f));
+    } else {
+        p = dup(5.989100318e-04f);
+        p = fma2(p, y, dup(3.099172190e-02f));
+        p = fma2(p, y, dup(3.629413843e-01f));
+        p = fma2(p, y, dup(1.422382593e+00f));
+        p = fma2(p, y, dup(2.092346668e+00f));
+        p = fma2(p, y, dup(1.0f));
+    }
     return p;
 }
 
@@ -457,10 +509,11 @@ __device__ __forceinline__ Geo2 geometry_x2(f2 x, f2 y, f2 S, f2 Yq)
 }
 
 // Per-branch formulas of accel_m for both lanes (FP32, the same operations).
+template <bool NARROW>
 __device__ __forceinline__ f2 m_rational_x2(const Geo2& g, f2 T, const HaloX2& hc)
 {
-    const f2 nr = mul2(nfw_N_x2(g.ys), mul2(g.rs, T));
-    const f2 d = nfw_D_x2(g.ys);
+    const f2 nr = mul2(nfw_N_x2<NARROW>(g.ys), mul2(g.rs, T));
+    const f2 d = nfw_D_x2<NARROW>(g.ys);
     return fma2(nr, pk(rcp_approx(f2lo(d)), rcp_approx(f2hi(d))), hc.neg_invR3);
 }
 __device__ __forceinline__ f2 m_log_x2(const Geo2& g, f2 rinv2, const HaloX2& hc)
@@ -480,10 +533,11 @@ __device__ __forceinline__ f2 m_out_x2(const Geo2& g, const HaloX2& hc)
 }
 // any mix of branches: each formula that some lane of the warp needs,
 // evaluated for both lanes and selected per lane
+template <bool NARROW>
 __device__ __forceinline__ f2 m_mixed_x2(const Geo2& g, f2 T, const HaloX2& hc, bool need_log)
 {
     const f2 rinv2 = mul2(g.rinv, g.rinv);
-    const f2 mq = m_rational_x2(g, T, hc);
+    const f2 mq = m_rational_x2<NARROW>(g, T, hc);
     const f2 ml = need_log ? m_log_x2(g, rinv2, hc) : dup(0.0f);
     const f2 ms = m_shell_x2(g, rinv2, hc);
     const bool n0 = f2lo(g.ys) < hc.c, n1 = f2hi(g.ys) < hc.c;
@@ -503,6 +557,7 @@ __device__ __forceinline__ f2 m_mixed_x2(const Geo2& g, f2 T, const HaloX2& hc, 
 // beyond R), or any mix (each formula that a lane needs evaluated for all and
 // selected per lane).  All lanes of the warp execute this function together
 // (the integration loop is warp-uniform).
+template <bool NARROW>
 __device__ __forceinline__ void accel_m_pair_x2(f2 xa, f2 ya, f2 Sa, f2 Ya, f2 Ta,
                                                 f2 xb, f2 yb, f2 Sb, f2 Yb, f2 Tb,
                                                 const HaloX2& hc, f2& ma, f2& mb)
@@ -511,8 +566,8 @@ __device__ __forceinline__ void accel_m_pair_x2(f2 xa, f2 ya, f2 Sa, f2 Ya, f2 T
     const Geo2 gb = geometry_x2(xb, yb, Sb, Yb);
     const unsigned full = 0xffffffffu;
     if (__all_sync(full, ga.q0 && ga.q1 && gb.q0 && gb.q1)) {
-        ma = m_rational_x2(ga, Ta, hc);
-        mb = m_rational_x2(gb, Tb, hc);
+        ma = m_rational_x2<NARROW>(ga, Ta, hc);
+        mb = m_rational_x2<NARROW>(gb, Tb, hc);
         return;
     }
     // lanes inside R and inside the NFW edge
@@ -529,8 +584,8 @@ __device__ __forceinline__ void accel_m_pair_x2(f2 xa, f2 ya, f2 Sa, f2 Ya, f2 T
     const bool la = (na0 && !ga.q0) || (na1 && !ga.q1);
     const bool lb = (nb0 && !gb.q0) || (nb1 && !gb.q1);
     const bool need_log = __any_sync(full, la || lb);
-    ma = m_mixed_x2(ga, Ta, hc, need_log);
-    mb = m_mixed_x2(gb, Tb, hc, need_log);
+    ma = m_mixed_x2<NARROW>(ga, Ta, hc, need_log);
+    mb = m_mixed_x2<NARROW>(gb, Tb, hc, need_log);
 }
 
 // One 16-byte entry of the duplicated table (two slots, each a {c, c} pair).
@@ -547,7 +602,7 @@ __device__ __forceinline__ ulonglong2 coef_pair(const uint4* src4, int q)
 // loaded where it is first needed, which keeps the table out of registers.
 // The four force evaluations run as two independent pairs (stages 1 and 2,
 // then 3 and 4); every value is formed by the same operations as in rk4_step.
-template <bool GTAB>
+template <bool GTAB, bool NARROW>
 __device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const uint4* src4,
                                             const HaloX2& hc)
 {
@@ -558,7 +613,7 @@ __device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const 
     const ulonglong2 q7 = coef_pair<GTAB>(src4, 7), q8 = coef_pair<GTAB>(src4, 8);
     const f2 S0{q5.x}, S1{q5.y}, Yq0{q6.y}, Yq1{q7.x}, T0{q8.x}, T1{q8.y};
     f2 m1, m2;
-    accel_m_pair_x2(x, y, S0, Yq0, T0, X2, Y2, S1, Yq1, T1, hc, m1, m2);
+    accel_m_pair_x2<NARROW>(x, y, S0, Yq0, T0, X2, Y2, S1, Yq1, T1, hc, m1, m2);
     const ulonglong2 q1 = coef_pair<GTAB>(src4, 1), q2 = coef_pair<GTAB>(src4, 2);
     const f2 MA3{q1.x}, B1{q1.y}, B2{q2.x};
     const f2 p1 = mul2(B1, m1);
@@ -571,7 +626,7 @@ __device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const 
     const ulonglong2 q9 = coef_pair<GTAB>(src4, 9);
     const f2 S2{q6.x}, Yq2{q7.y}, T2{q9.x};
     f2 m3, m4;
-    accel_m_pair_x2(X3, Y3, S1, Yq1, T1, X4, Y4, S2, Yq2, T2, hc, m3, m4);
+    accel_m_pair_x2<NARROW>(X3, Y3, S1, Yq1, T1, X4, Y4, S2, Yq2, T2, hc, m3, m4);
     const ulonglong2 q3 = coef_pair<GTAB>(src4, 3), q4 = coef_pair<GTAB>(src4, 4);
     const f2 B3{q2.y}, B4{q3.x}, W0{q3.y}, W1{q4.x}, W2{q4.y};
     const f2 p3 = mul2(B3, m3);
@@ -588,6 +643,30 @@ __device__ __forceinline__ void rk4_step_x2(f2& x, f2& y, f2& vx, f2& vy, const 
     vy = fma2(p4, Y4, fma2(ty, third, vy));
     x = nx;
     y = ny;
+}
+
+// The packed step loop of one tile for steps [s_begin, s_end): early-exit test
+// every kExitEvery steps, then an RK4 step of both lanes.  NARROW is fixed per
+// request (the rational fit its force uses), so the tile chooses the loop once.
+template <bool GTAB, bool NARROW>
+__device__ __forceinline__ void packed_steps(f2& X, f2& Y, f2& VX, f2& VY, const float* tab,
+                                             int s_begin, int s_end, bool act0, bool act1,
+                                             bool done, const HaloX2& h2, float R)
+{
+    for (int n = s_begin; n < s_end; ++n) {
+        if (((n - s_begin) & (kExitEvery - 1)) == 0) {
+            const f2 r2 = fma2(X, X, mul2(Y, Y));
+            const f2 dot = fma2(X, VX, mul2(Y, VY));
+            const f2 v2 = fma2(VX, VX, mul2(VY, VY));
+            const float irem = tab[(size_t)n * 2 * C_COUNT + 2 * C_IREM];
+            const bool fin0 = !act0 || escapes(f2lo(r2), f2lo(dot), f2lo(v2), h2.R2, R, irem);
+            const bool fin1 = !act1 || escapes(f2hi(r2), f2hi(dot), f2hi(v2), h2.R2, R, irem);
+            done |= fin0 && fin1;
+            if (__all_sync(0xffffffffu, done)) break;
+        }
+        rk4_step_x2<GTAB, NARROW>(X, Y, VX, VY,
+                                  reinterpret_cast<const uint4*>(tab + (size_t)n * 2 * C_COUNT), h2);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -763,20 +842,13 @@ traj_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ tile_p
             f2 X = pk(x[0], x[1]), Y = pk(y[0], y[1]);
             f2 VX = pk(vx[0], vx[1]), VY = pk(vy[0], vy[1]);
             const HaloX2 h2{dup(hc.invIc), dup(-hc.invR3), hc.R2, hc.c};
-            for (int n = s_begin; n < s_end; ++n) {
-                if (((n - s_begin) & (kExitEvery - 1)) == 0) {
-                    const f2 r2 = fma2(X, X, mul2(Y, Y));
-                    const f2 dot = fma2(X, VX, mul2(Y, VY));
-                    const f2 v2 = fma2(VX, VX, mul2(VY, VY));
-                    const float irem = tab[(size_t)n * 2 * C_COUNT + 2 * C_IREM];
-                    const bool fin0 = !act[0] || escapes(f2lo(r2), f2lo(dot), f2lo(v2), hc.R2, hc.R, irem);
-                    const bool fin1 = !act[1] || escapes(f2hi(r2), f2hi(dot), f2hi(v2), hc.R2, hc.R, irem);
-                    done |= fin0 && fin1;
-                    if (__all_sync(0xffffffffu, done)) break;
-                }
-                rk4_step_x2<GTAB>(X, Y, VX, VY,
-                                  reinterpret_cast<const uint4*>(tab + (size_t)n * 2 * C_COUNT), h2);
-            }
+            const float* ftab = reinterpret_cast<const float*>(tab);
+            if (hc.narrow)
+                packed_steps<GTAB, true>(X, Y, VX, VY, ftab, s_begin, s_end, act[0], act[1], done,
+                                         h2, hc.R);
+            else
+                packed_steps<GTAB, false>(X, Y, VX, VY, ftab, s_begin, s_end, act[0], act[1], done,
+                                          h2, hc.R);
             x[0] = f2lo(X); x[1] = f2hi(X);
             y[0] = f2lo(Y); y[1] = f2hi(Y);
             vx[0] = f2lo(VX); vx[1] = f2hi(VX);
