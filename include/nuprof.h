@@ -184,7 +184,9 @@ typedef struct nu_opts {
     int block;           /* threads per CTA: 0 (default 256) or 64..512, multiple of 32 */
     int tpt;             /* trajectories per thread: 0 (default 1), 1, 2, or 3 =
                             two per thread in packed FP32x2 arithmetic (mixed
-                            precision; results bitwise those of 2)             */
+                            precision; results bitwise those of 2).  The fastest
+                            mixed-precision shape on GB300 is block 128, tpt 3
+                            with NU_FLAG_GTAB; nu_autotune finds it            */
     int flags;           /* NU_FLAG_*                                             */
     nu_alloc_fn alloc;
     nu_free_fn free;
