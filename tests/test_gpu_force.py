@@ -22,8 +22,10 @@ def gpu():
 
 
 @pytest.mark.parametrize("prec,tol", [(W.FP64, 1e-13), (W.MIXED, 1e-6)])
-@pytest.mark.parametrize("M,c", [(1e11, 12.0), (1e13, 7.0), (1e15, 4.0)])
+@pytest.mark.parametrize("M,c", [(1e11, 12.0), (1e13, 7.0), (1e15, 4.0), (1e12, 8.0), (1e12, 16.0)])
 def test_force_matches_oracle(prec, tol, M, c):
+    """c = 8 and c = 16 put the NFW edge at the end of the narrow and of the wide
+    rational fit of the FP32 force."""
     pb = W.plain_small(precision=prec)[0].replace(M_h=M, c=c, xi_kind=W.XI_STATIC, n_steps=40)
     d = oracle.derive(pb)
     h = nu.create(pb)
