@@ -619,12 +619,13 @@ def bench_ours(args):
             misses = []
             for i, e in zip(sel, rel):
                 if e > tol:
-                    # the oracle's own spread at this radius under FP32 state rounding,
-                    # rounding-size step noise and a relative force error of the same
-                    # size (two seeds, one of each sign)
-                    spr = max(abs(_oracle.profile_perturbed(pb.replace(precision=W.MIXED), 2.0 ** -22,
+                    # the oracle's own spread at this radius under rounding-size step
+                    # noise and a relative force error of the same size (two seeds, one
+                    # of each sign), with the state rounded to FP32 in the mixed mode
+                    mixed = prec == W.MIXED
+                    spr = max(abs(_oracle.profile_perturbed(pb, 2.0 ** -22 if mixed else 2.0 ** -50,
                                                             seed, radius_sel=[i], step_noise=True,
-                                                            force_noise=True, round_state=True)[i]
+                                                            force_noise=True, round_state=mixed)[i]
                                   - r[i]) / abs(r[i]) for seed in (1, 2))
                     misses.append({"radius": int(i), "rel_err": float(e), "oracle_spread": spr})
             accuracy["per_mass"][f"{pb.m_eV:g} eV"] = {
